@@ -1,0 +1,196 @@
+/*
+ * hbe.h -- C ABI of libhbe, a GB300 (sm_103a) solver for the Higgs boson
+ * equation (HBE) in de Sitter spacetime,
+ *
+ *     phi_tt - e^{-2t} Delta phi + 3 phi_t = mu^2 phi - lambda phi^3,          (Sec. 1, Eq. HBE)
+ *     phi(x, t0) = phi0(x),  phi_t(x, t0) = phi1(x),                          (Eq. HBEinit)
+ *
+ * discretised as in Sec. 2.1 of Balogh, Banda & Yagdjian (arXiv:1803.01291):
+ * the cube of side L centred at the origin (the paper's unit box with the
+ * factor 1/L^2, Eq. higgs-boson-rescalled), a uniform grid of N^3 unknowns,
+ * the 13-point fourth-order finite-difference Laplacian (Sec. 2.1), the
+ * first-order system v = (phi, psi = phi_t) with right-hand side Eq. (rhs),
+ * and the classic explicit fourth-order Runge-Kutta step (Sec. 2.1).
+ *
+ * Conventions shared by every entry point
+ *   - Grid: zero-Dirichlet (Eq. BC): h = L/(N+1), node i at (i - (N-1)/2) h,
+ *     phi = psi = 0 on the two ghost layers outside the box.  Periodic: h = L/N,
+ *     node i at (i - N/2) h, neighbours wrap.
+ *   - Host/device arrays of a field are N^3 doubles, x fastest:
+ *     element (x, y, z) at index (z*N + y)*N + x.
+ *   - Sign masks: N*N*W uint32 words, W = ceil(N/32); bit (x % 32) of word
+ *     (z*N + y)*W + x/32 is set where the condition holds.
+ *   - Time: t_n = t0 + n*dt in double precision (no running sum); the RK4
+ *     stage times are t_n, t_n + dt/2, t_n + dt/2, t_n + dt (Sec. 2.1).
+ *   - Every call returns an hbe_status; nothing throws or aborts.  After an
+ *     error, hbe_last_error() describes it.  A context is used by one host
+ *     thread at a time.  No call keeps a pointer to caller memory.
+ *   - Device memory for the fields is allocated by hbe_create (cudaMalloc)
+ *     unless the caller hands a buffer of hbe_workspace_bytes() bytes to
+ *     hbe_create_in, which then allocates nothing on the device for fields.
+ */
+#ifndef HBE_H_
+#define HBE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hbe_ctx hbe_ctx;
+typedef struct hbe_batch hbe_batch;
+
+typedef enum {
+  HBE_OK = 0,
+  HBE_EINVAL = 1,    /* bad argument (size, pointer, parameter) */
+  HBE_ENOMEM = 2,    /* device or host allocation failed */
+  HBE_ECUDA = 3,     /* a CUDA call failed; see hbe_last_error */
+  HBE_ESTATE = 4,    /* call out of order (e.g. step before set_initial) */
+  HBE_STOPPED = 5,   /* stepping stopped early: max|phi| passed the stop threshold */
+  HBE_NONFINITE = 6, /* stepping stopped early: phi became NaN or infinite */
+  HBE_ETIMEOUT = 7   /* a bounded device wait expired; the context state is undefined */
+} hbe_status;
+
+typedef enum { HBE_BC_DIRICHLET0 = 0, HBE_BC_PERIODIC = 1 } hbe_bc;
+
+/* Arithmetic of the stepping path.  t, e^{-2t}/h^2 and the stage coefficients
+ * are always formed in double precision on the device.
+ *   HBE_FP64       fields and arithmetic in binary64.
+ *   HBE_FP32       fields and arithmetic in binary32; phi and psi carried as
+ *                  compensated (hi, lo) float pairs, updated by TwoSum.
+ *   HBE_BF16       as HBE_FP32, but the stage right-hand sides G1..G3 are
+ *                  stored as bfloat16 (round to nearest even).
+ *   HBE_FP32_PLAIN binary32 throughout, no compensation (ablation). */
+typedef enum { HBE_FP64 = 0, HBE_FP32 = 1, HBE_BF16 = 2, HBE_FP32_PLAIN = 3 } hbe_prec;
+
+typedef struct {
+  double t;            /* time of the state the diagnostics describe */
+  int64_t step;        /* steps taken since the last set_initial/load */
+  double max_abs_phi;  /* max over the N^3 unknowns of |phi| (NaN/inf count as +inf) */
+  int32_t finite;      /* 1 if every phi value is finite */
+  int32_t reserved;
+  int64_t n_pos;       /* 6-connected components of {phi > eps} (wrapping if periodic) */
+  int64_t n_neg;       /* same for {phi < -eps} */
+  int64_t bubble_count;/* max(0, n_pos + n_neg - 1): maximal connected sets across
+                          which phi changes sign (the bubble definition of Sec. 1) */
+} hbe_diag_t;
+
+/* Tile configuration of the stage kernels (see hbe_variant_info). */
+typedef struct {
+  int32_t tile_x, tile_y;   /* x-y tile of one thread block */
+  int32_t threads;          /* threads per block */
+  int32_t smem_bytes[4];    /* dynamic shared memory per stage kernel */
+  int32_t ring[4];          /* z-planes in the TMA ring per stage kernel */
+} hbe_variant_t;
+
+/* ---- Solver context --------------------------------------------------- */
+
+/* Bytes of device memory the fields of one context need (for hbe_create_in). */
+hbe_status hbe_workspace_bytes(int N, int bc, int prec, size_t *bytes);
+
+/* Create a solver for the N^3 problem on the box of side L with parameters
+ * mu >= 0 and lambda (any sign; lambda < 0 is the focusing case, Sec. 3
+ * Example blow-up).  Requires N >= 8 (periodic: N >= 8 as well), L > 0.
+ * Allocates the fields on the current CUDA device.  *out receives the
+ * context; it is owned by the library and released by hbe_destroy. */
+hbe_status hbe_create(int N, double L, double mu, double lambda, int bc, int prec,
+                      hbe_ctx **out);
+
+/* As hbe_create, but the fields live in the caller's device buffer
+ * d_workspace of at least hbe_workspace_bytes() bytes, 256-byte aligned.  The
+ * buffer must stay valid until hbe_destroy; the library never frees it. */
+hbe_status hbe_create_in(int N, double L, double mu, double lambda, int bc, int prec,
+                         void *d_workspace, size_t bytes, hbe_ctx **out);
+
+void hbe_destroy(hbe_ctx *ctx);
+
+/* Stream (cudaStream_t) every later call of this context enqueues on; NULL
+ * is the legacy default stream. */
+hbe_status hbe_set_stream(hbe_ctx *ctx, void *stream);
+
+/* Tile variant (index into hbe_variant_info's table for this precision) and
+ * z-chunk length (planes per block work item; 0 = whole column). */
+hbe_status hbe_set_tuning(hbe_ctx *ctx, int variant, int zchunk);
+hbe_status hbe_variant_info(int prec, int variant, hbe_variant_t *out);
+int hbe_variant_count(int prec);
+
+/* Initial data (Eq. HBEinit) at time t0: host arrays of N^3 doubles, copied. */
+hbe_status hbe_set_initial(hbe_ctx *ctx, const double *phi0, const double *phi1, double t0);
+/* Same from device arrays (read on the context's stream before return). */
+hbe_status hbe_set_initial_device(hbe_ctx *ctx, const double *d_phi0, const double *d_phi1,
+                                  double t0);
+
+/* Stop stepping after the first step whose max|phi| exceeds threshold
+ * (0 disables; a non-finite phi always stops). */
+hbe_status hbe_set_stop(hbe_ctx *ctx, double threshold);
+
+/* Advance by nsteps RK4 steps of size dt > 0 (Sec. 2.1).  Blocks until done.
+ * Returns HBE_STOPPED / HBE_NONFINITE when the stop rule ended it early; the
+ * state is then the one after the step that triggered it.  Changing dt
+ * between calls restarts the time origin at the current t. */
+hbe_status hbe_step(hbe_ctx *ctx, int64_t nsteps, double dt);
+
+/* Enqueue nsteps steps on the context's stream without waiting; the stop
+ * rule still applies on the device.  hbe_sync waits and reports status. */
+hbe_status hbe_step_async(hbe_ctx *ctx, int64_t nsteps, double dt);
+hbe_status hbe_sync(hbe_ctx *ctx);
+
+/* Current state to host arrays of N^3 doubles (psi may be NULL) and time. */
+hbe_status hbe_read(hbe_ctx *ctx, double *phi, double *psi, double *t);
+/* Same to device arrays on the context's stream (not synchronised). */
+hbe_status hbe_read_device(hbe_ctx *ctx, double *d_phi, double *d_psi);
+/* Profiling aid: nsteps (1..4096) RK4 steps with the four stage kernels
+ * launched one at a time (no graph) and each bracketed by CUDA events on the
+ * context's stream; ms_per_stage[s] receives the mean duration of stage s+1
+ * (4 floats, caller-owned).  The state advances as with hbe_step.  Blocks. */
+hbe_status hbe_profile_stages(hbe_ctx *ctx, int64_t nsteps, double dt, float *ms_per_stage);
+
+/* Steps taken and current time. */
+hbe_status hbe_progress(hbe_ctx *ctx, int64_t *steps, double *t);
+
+/* Diagnostics of the current phi (Sec. 1 bubbles; Sec. 3 uses max|phi|):
+ * sign masks of {phi > eps} and {phi < -eps} (host buffers of N*N*W words,
+ * either may be NULL) and the component counts.  Blocks. */
+hbe_status hbe_diag(hbe_ctx *ctx, double eps, hbe_diag_t *out, uint32_t *pos_mask,
+                    uint32_t *neg_mask);
+
+/* Raw state (both fields in storage precision, step count, t0, dt) to/from
+ * a file; a load into a context of the same N, bc and precision continues
+ * bit for bit. */
+hbe_status hbe_save(hbe_ctx *ctx, const char *path);
+hbe_status hbe_load(hbe_ctx *ctx, const char *path);
+
+const char *hbe_last_error(const hbe_ctx *ctx);
+const char *hbe_status_string(int status);
+
+/* Number of stage-kernel launches this context (or batch) has enqueued. */
+int64_t hbe_launch_count(const hbe_ctx *ctx);
+
+/* ---- Batched stepping (continuous batching) ---------------------------- */
+/* A batch advances many contexts of one precision together: every RK4 stage
+ * is one persistent kernel launch over the tiles of all members, and K steps
+ * are replayed as one CUDA graph.  Members join and leave between runs
+ * without re-capturing the graph.  A member's per-point arithmetic is the same
+ * as when it steps alone, so its results are bitwise identical.  */
+
+/* K = steps per run (1..64).  stream as in hbe_set_stream. */
+hbe_status hbe_batch_create(int prec, int K, void *stream, hbe_batch **out);
+void hbe_batch_destroy(hbe_batch *b);
+/* Admit ctx (same precision, state set) with nsteps more steps of size dt. */
+hbe_status hbe_batch_add(hbe_batch *b, hbe_ctx *ctx, int64_t nsteps, double dt);
+/* Remove a member (finished or not); its state stays readable. */
+hbe_status hbe_batch_remove(hbe_batch *b, hbe_ctx *ctx);
+/* One run: up to K steps for every member.  On return *n_finished holds how
+ * many members reached their step count or stopped, listed in finished[]
+ * (capacity max_finished); they are removed from the batch. */
+hbe_status hbe_batch_run(hbe_batch *b, hbe_ctx **finished, int max_finished, int *n_finished);
+int hbe_batch_size(const hbe_batch *b);
+const char *hbe_batch_last_error(const hbe_batch *b);
+int64_t hbe_batch_launch_count(const hbe_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HBE_H_ */

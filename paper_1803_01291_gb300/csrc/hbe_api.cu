@@ -1,0 +1,1099 @@
+// hbe_api.cu -- the C ABI of libhbe (include/hbe.h): contexts, device memory,
+// TMA descriptors, work lists, CUDA-graph stepping, diagnostics, checkpoints
+// and the batched (continuous-batching) runner.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "hbe.h"
+#include "hbe_aux.h"
+#include "hbe_common.cuh"
+#include "hbe_variants.h"
+
+using namespace hbe;
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+std::mutex g_attr_mu;
+std::set<const void *> g_attr_done;
+
+const VariantTable &table_for(int prec) {
+  switch (prec) {
+    case HBE_FP64: return variants_fp64();
+    case HBE_FP32: return variants_fp32();
+    case HBE_BF16: return variants_bf16();
+    default: return variants_fp32_plain();
+  }
+}
+
+int state_size(int prec) { return prec == HBE_FP64 ? 8 : 4; }
+int g_size(int prec) { return prec == HBE_FP64 ? 8 : (prec == HBE_BF16 ? 2 : 4); }
+bool is_kahan(int prec) { return prec == HBE_FP32 || prec == HBE_BF16; }
+
+CUtensorMapDataType tm_type(int esize) {
+  return esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                    : (esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+}
+
+int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+}  // namespace
+
+struct hbe_ctx {
+  int N = 0, bc = 0, prec = 0;
+  double L = 0, mu = 0, lambda = 0, h = 0;
+  int device = 0, sms = 0;
+  cudaStream_t stream = nullptr;      // user stream (work is enqueued here)
+  cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
+  int variant = 0, zchunk = 0;
+  int hxs = 0, hxg = 0, pitch_s = 0, pitch_g = 0;
+  int64_t plane_s = 0, plane_g = 0;
+  size_t bytes_s = 0, bytes_g = 0, ws_bytes = 0;
+  void *ws = nullptr;
+  bool own_ws = false;
+  void *f[NUM_FIELDS] = {};
+  CUtensorMap *d_tmaps = nullptr;
+  unsigned long long *d_maxabs = nullptr;
+  Desc *d_desc = nullptr;
+  Desc *h_desc = nullptr;  // pinned mirror
+  WorkItem *d_items = nullptr;
+  int *d_nitems = nullptr;
+  int *d_one = nullptr;
+  int nitems = 0, items_cap = 0;
+  int grid[4] = {0, 0, 0, 0};
+  unsigned *d_err = nullptr;
+  int K = 8;
+  cudaGraphExec_t gexec = nullptr;
+  double *d_stage = nullptr;
+  size_t stage_elems = 0;
+  uint32_t *d_masks = nullptr;
+  int *d_labels = nullptr;
+  unsigned long long *d_counts = nullptr;
+  bool has_state = false;
+  bool pending = false;        // device work enqueued since the last sync
+  bool desc_stale = false;     // device descriptor older than the host mirror
+  bool in_batch = false;
+  int64_t launches = 0;
+  std::string err;
+};
+
+struct hbe_batch {
+  int prec = 0, K = 8, sms = 0, device = 0;
+  cudaStream_t stream = nullptr, cap_stream = nullptr;
+  std::vector<hbe_ctx *> members;
+  Desc *d_descs = nullptr, *h_descs = nullptr;
+  int *d_ndesc = nullptr;
+  int cap_desc = 0;
+  struct List {
+    WorkItem *d_items = nullptr;
+    int *d_n = nullptr;
+    int cap = 0;
+    int grid[4] = {0, 0, 0, 0};
+  } lists[kMaxVariants];
+  int nvariants = 0;
+  unsigned *d_err = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool dirty = true;
+  int64_t launches = 0;
+  std::string err;
+};
+
+namespace {
+
+hbe_status set_err(std::string &dst, hbe_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  dst = buf;
+  return st;
+}
+
+#define CKX(dst, call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return set_err(dst, e_ == cudaErrorMemoryAllocation ? HBE_ENOMEM : HBE_ECUDA,        \
+                     "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,       \
+                     __LINE__);                                                              \
+  } while (0)
+#define CK(call) CKX(ctx->err, call)
+
+hbe_status prepare_kernel(std::string &err, const KernelInfo &ki) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (g_attr_done.count(ki.fn)) return HBE_OK;
+  CKX(err, cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ki.smem));
+  g_attr_done.insert(ki.fn);
+  return HBE_OK;
+}
+
+hbe_status persistent_grid(std::string &err, const KernelInfo &ki, int sms, int *out) {
+  hbe_status st = prepare_kernel(err, ki);
+  if (st != HBE_OK) return st;
+  int nb = 0;
+  CKX(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ki.fn, ki.threads, ki.smem));
+  if (nb < 1) return set_err(err, HBE_ECUDA, "stage kernel does not fit on an SM");
+  *out = nb * sms;
+  return HBE_OK;
+}
+
+hbe_status get_encoder(std::string &err) {
+  std::call_once(g_encode_once, [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!g_encode) return set_err(err, HBE_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  return HBE_OK;
+}
+
+// 3D map over a padded field: dims (pitch, N + 4, N), box (bx, by, 1).
+hbe_status encode_map(hbe_ctx *ctx, CUtensorMap *m, void *base, int esize, int pitch, int bx,
+                      int by) {
+  cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)(ctx->N + 4), (cuuint64_t)ctx->N};
+  cuuint64_t strides[2] = {(cuuint64_t)pitch * esize, (cuuint64_t)pitch * (ctx->N + 4) * esize};
+  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(m, tm_type(esize), 3, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return set_err(ctx->err, HBE_ECUDA, "cuTensorMapEncodeTiled failed (%d), box %dx%d", (int)r,
+                   bx, by);
+  return HBE_OK;
+}
+
+int auto_zchunk(int N, int columns, int resident) {
+  if (columns >= 2 * resident) return N;
+  int nz = (2 * resident + columns - 1) / columns;
+  int zc = (N + nz - 1) / nz;
+  return std::max(zc, std::min(N, 16));
+}
+
+// Work items of one context, ordered z-chunk, then y, then x (neighbouring
+// tiles run together, so halo rows are still in L2 when they are read).
+void build_items(const hbe_ctx *ctx, int member, int zchunk, std::vector<WorkItem> &out) {
+  const KernelInfo &ki = table_for(ctx->prec).k[ctx->variant][0];
+  const int tx = (ctx->N + ki.tx - 1) / ki.tx, ty = (ctx->N + ki.ty - 1) / ki.ty;
+  for (int z0 = 0; z0 < ctx->N; z0 += zchunk)
+    for (int j = 0; j < ty; ++j)
+      for (int i = 0; i < tx; ++i)
+        out.push_back(make_int4(member, i | (j << 16), z0, std::min(zchunk, ctx->N - z0)));
+}
+
+hbe_status apply_tuning(hbe_ctx *ctx, int variant, int zchunk) {
+  const VariantTable &vt = table_for(ctx->prec);
+  if (variant < 0 || variant >= vt.count)
+    return set_err(ctx->err, HBE_EINVAL, "variant %d out of range [0, %d)", variant, vt.count);
+  if (zchunk < 0) return set_err(ctx->err, HBE_EINVAL, "zchunk must be >= 0");
+  const KernelInfo *ks = vt.k[variant];
+  ctx->variant = variant;
+  // tensor maps for this tile shape
+  const int es = state_size(ctx->prec), eg = g_size(ctx->prec);
+  const int tx = ks[0].tx, ty = ks[0].ty;
+  const int bxs = tx + 2 * ctx->hxs, bxg = tx + 2 * ctx->hxg, by = ty + 4;
+  CUtensorMap maps[NUM_TMAPS];
+  memset(maps, 0, sizeof(maps));
+  hbe_status st;
+  auto E = [&](int idx, int field, int esz, int pitch, int bx, int byy) {
+    void *base = ctx->f[field] ? ctx->f[field] : ctx->f[F_P0];  // unused maps point at p
+    return encode_map(ctx, &maps[idx], base, esz, pitch, bx, byy);
+  };
+  if ((st = E(TM_P_H0, F_P0, es, ctx->pitch_s, bxs, by))) return st;
+  if ((st = E(TM_P_H1, F_P1, es, ctx->pitch_s, bxs, by))) return st;
+  if ((st = E(TM_Q_H0, F_Q0, es, ctx->pitch_s, bxs, by))) return st;
+  if ((st = E(TM_Q_H1, F_Q1, es, ctx->pitch_s, bxs, by))) return st;
+  if ((st = E(TM_Q_I0, F_Q0, es, ctx->pitch_s, tx, ty))) return st;
+  if ((st = E(TM_Q_I1, F_Q1, es, ctx->pitch_s, tx, ty))) return st;
+  if ((st = E(TM_PLO_I0, F_PLO0, es, ctx->pitch_s, tx, ty))) return st;
+  if ((st = E(TM_PLO_I1, F_PLO1, es, ctx->pitch_s, tx, ty))) return st;
+  if ((st = E(TM_QLO_I0, F_QLO0, es, ctx->pitch_s, tx, ty))) return st;
+  if ((st = E(TM_QLO_I1, F_QLO1, es, ctx->pitch_s, tx, ty))) return st;
+  if ((st = E(TM_G1_H, F_G1, eg, ctx->pitch_g, bxg, by))) return st;
+  if ((st = E(TM_G1_I, F_G1, eg, ctx->pitch_g, tx, ty))) return st;
+  if ((st = E(TM_G2_H, F_G2, eg, ctx->pitch_g, bxg, by))) return st;
+  if ((st = E(TM_G2_I, F_G2, eg, ctx->pitch_g, tx, ty))) return st;
+  if ((st = E(TM_G3_I, F_G3, eg, ctx->pitch_g, tx, ty))) return st;
+  CK(cudaMemcpy(ctx->d_tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice));
+  // persistent grid per stage and the work list
+  int resident = 1 << 30;
+  for (int s = 0; s < 4; ++s) {
+    if ((st = persistent_grid(ctx->err, ks[s], ctx->sms, &ctx->grid[s]))) return st;
+    resident = std::min(resident, ctx->grid[s]);
+  }
+  const int columns = ((ctx->N + tx - 1) / tx) * ((ctx->N + ty - 1) / ty);
+  ctx->zchunk = zchunk > 0 ? std::min(zchunk, ctx->N) : auto_zchunk(ctx->N, columns, resident);
+  std::vector<WorkItem> items;
+  build_items(ctx, 0, ctx->zchunk, items);
+  if ((int)items.size() > ctx->items_cap) {
+    if (ctx->d_items) cudaFree(ctx->d_items);
+    ctx->d_items = nullptr;
+    CK(cudaMalloc(&ctx->d_items, items.size() * sizeof(WorkItem)));
+    ctx->items_cap = (int)items.size();
+  }
+  ctx->nitems = (int)items.size();
+  CK(cudaMemcpy(ctx->d_items, items.data(), items.size() * sizeof(WorkItem),
+                cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_nitems, &ctx->nitems, sizeof(int), cudaMemcpyHostToDevice));
+  for (int s = 0; s < 4; ++s) ctx->grid[s] = std::min(ctx->grid[s], ctx->nitems);
+  if (ctx->gexec) {
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+  }
+  return HBE_OK;
+}
+
+hbe_status launch_stage(std::string &err, const KernelInfo &ki, int grid, const StageParams &p,
+                        cudaStream_t st) {
+  StageParams prm = p;
+  void *args[] = {&prm};
+  CKX(err, cudaLaunchKernel(ki.fn, dim3(grid), dim3(ki.threads), args, ki.smem, st));
+  return HBE_OK;
+}
+
+hbe_status ensure_graph(hbe_ctx *ctx) {
+  if (ctx->gexec) return HBE_OK;
+  const VariantTable &vt = table_for(ctx->prec);
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+  hbe_status st = HBE_OK;
+  for (int k = 0; k < ctx->K && st == HBE_OK; ++k)
+    for (int s = 0; s < 4 && st == HBE_OK; ++s) {
+      StageParams p{ctx->d_desc, ctx->d_items, ctx->d_nitems, ctx->d_err, k};
+      st = launch_stage(ctx->err, vt.k[ctx->variant][s], ctx->grid[s], p, ctx->cap_stream);
+    }
+  cudaError_t e = launch_advance(ctx->d_desc, ctx->d_one, 1, ctx->K, ctx->cap_stream);
+  cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
+  if (st != HBE_OK) return st;
+  CK(e);
+  CK(e2);
+  e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  return HBE_OK;
+}
+
+hbe_status ensure_stage_buffer(hbe_ctx *ctx) {
+  if (ctx->d_stage) return HBE_OK;
+  const size_t plane = (size_t)ctx->N * ctx->N;
+  size_t planes = std::max<size_t>(1, (size_t)(8u << 20) / plane);  // <= 64 MiB of doubles
+  planes = std::min<size_t>(planes, (size_t)ctx->N);
+  ctx->stage_elems = planes * plane;
+  CK(cudaMalloc(&ctx->d_stage, 2 * ctx->stage_elems * sizeof(double)));
+  return HBE_OK;
+}
+
+hbe_status sync_ctx(hbe_ctx *ctx) {
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->pending) {
+    CK(cudaMemcpy(ctx->h_desc, ctx->d_desc, sizeof(Desc), cudaMemcpyDeviceToHost));
+    ctx->pending = false;
+  }
+  unsigned e = 0;
+  CK(cudaMemcpy(&e, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (e & DEV_ERR_TIMEOUT)
+    return set_err(ctx->err, HBE_ETIMEOUT, "a stage kernel's TMA wait timed out");
+  if (e & DEV_ERR_UNIONFIND)
+    return set_err(ctx->err, HBE_ETIMEOUT, "connected-component union did not converge");
+  return HBE_OK;
+}
+
+hbe_status push_desc(hbe_ctx *ctx) {
+  CK(cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(Desc), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->desc_stale = false;
+  return HBE_OK;
+}
+
+double current_t(const hbe_ctx *ctx) {
+  return ctx->h_desc->t0 + (double)ctx->h_desc->n_base * ctx->h_desc->dt;
+}
+
+hbe_status validate(std::string &err, int N, double L, double mu, double lambda, int bc, int prec) {
+  if (N < 8 || N > 2048) return set_err(err, HBE_EINVAL, "N=%d outside [8, 2048]", N);
+  if (!(L > 0.0) || !std::isfinite(L)) return set_err(err, HBE_EINVAL, "L must be finite and > 0");
+  if (!(mu >= 0.0) || !std::isfinite(mu)) return set_err(err, HBE_EINVAL, "mu must be finite and >= 0");
+  if (!std::isfinite(lambda)) return set_err(err, HBE_EINVAL, "lambda must be finite");
+  if (bc != HBE_BC_DIRICHLET0 && bc != HBE_BC_PERIODIC) return set_err(err, HBE_EINVAL, "bad bc %d", bc);
+  if (prec < HBE_FP64 || prec > HBE_FP32_PLAIN) return set_err(err, HBE_EINVAL, "bad precision %d", prec);
+  return HBE_OK;
+}
+
+void layout(int N, int prec, int *hxs, int *hxg, int *ps, int *pg, int64_t *pls, int64_t *plg,
+            size_t *bs, size_t *bg) {
+  const int es = state_size(prec), eg = g_size(prec);
+  *hxs = 16 / es;
+  *hxg = 16 / eg;
+  *ps = round_up(N + 2 * *hxs, *hxs);
+  *pg = round_up(N + 2 * *hxg, *hxg);
+  *pls = (int64_t)(N + 4) * *ps;
+  *plg = (int64_t)(N + 4) * *pg;
+  *bs = (size_t)(((size_t)*pls * N * es + 255) / 256 * 256);
+  *bg = (size_t)(((size_t)*plg * N * eg + 255) / 256 * 256);
+}
+
+size_t workspace_bytes(int N, int prec) {
+  int a, b, c, d;
+  int64_t e, f;
+  size_t bs, bg;
+  layout(N, prec, &a, &b, &c, &d, &e, &f, &bs, &bg);
+  const int nstate = is_kahan(prec) ? 8 : 4;
+  return nstate * bs + 3 * bg;
+}
+
+hbe_status create_common(int N, double L, double mu, double lambda, int bc, int prec, void *ws,
+                         size_t bytes, hbe_ctx **out) {
+  if (!out) return HBE_EINVAL;
+  *out = nullptr;
+  hbe_ctx *ctx = new hbe_ctx();
+  hbe_status st = validate(ctx->err, N, L, mu, lambda, bc, prec);
+  if (st == HBE_OK) st = get_encoder(ctx->err);
+  auto bail = [&](hbe_status s) {
+    hbe_destroy(ctx);
+    return s;
+  };
+  if (st != HBE_OK) return bail(st);
+  ctx->N = N; ctx->L = L; ctx->mu = mu; ctx->lambda = lambda; ctx->bc = bc; ctx->prec = prec;
+  ctx->h = bc == HBE_BC_PERIODIC ? L / N : L / (N + 1);
+  if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+    set_err(ctx->err, HBE_ECUDA, "no CUDA device");
+    return bail(HBE_ECUDA);
+  }
+  layout(N, prec, &ctx->hxs, &ctx->hxg, &ctx->pitch_s, &ctx->pitch_g, &ctx->plane_s,
+         &ctx->plane_g, &ctx->bytes_s, &ctx->bytes_g);
+  ctx->ws_bytes = workspace_bytes(N, prec);
+  if (ws) {
+    if (bytes < ctx->ws_bytes || (reinterpret_cast<uintptr_t>(ws) & 255u)) {
+      set_err(ctx->err, HBE_EINVAL, "workspace too small (%zu < %zu) or not 256-byte aligned",
+              bytes, ctx->ws_bytes);
+      return bail(HBE_EINVAL);
+    }
+    ctx->ws = ws;
+  } else {
+    if (cudaMalloc(&ctx->ws, ctx->ws_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->ws = nullptr;
+      set_err(ctx->err, HBE_ENOMEM, "cudaMalloc of %zu bytes failed", ctx->ws_bytes);
+      return bail(HBE_ENOMEM);
+    }
+    ctx->own_ws = true;
+  }
+  // carve the fields
+  char *p = static_cast<char *>(ctx->ws);
+  const int state_fields[] = {F_P0, F_P1, F_Q0, F_Q1, F_PLO0, F_PLO1, F_QLO0, F_QLO1};
+  const int nstate = is_kahan(prec) ? 8 : 4;
+  for (int i = 0; i < nstate; ++i) { ctx->f[state_fields[i]] = p; p += ctx->bytes_s; }
+  for (int i = 0; i < 3; ++i) { ctx->f[F_G1 + i] = p; p += ctx->bytes_g; }
+#define CKB(call)                                                                   \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      set_err(ctx->err, HBE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+      return bail(e_ == cudaErrorMemoryAllocation ? HBE_ENOMEM : HBE_ECUDA);        \
+    }                                                                               \
+  } while (0)
+  CKB(cudaMemset(ctx->ws, 0, ctx->ws_bytes));
+  CKB(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  CKB(cudaMalloc(&ctx->d_tmaps, NUM_TMAPS * sizeof(CUtensorMap)));
+  CKB(cudaMalloc(&ctx->d_maxabs, kMaxK * sizeof(unsigned long long)));
+  CKB(cudaMemset(ctx->d_maxabs, 0, kMaxK * sizeof(unsigned long long)));
+  CKB(cudaMalloc(&ctx->d_desc, sizeof(Desc)));
+  CKB(cudaMallocHost(&ctx->h_desc, sizeof(Desc)));
+  CKB(cudaMalloc(&ctx->d_nitems, sizeof(int)));
+  CKB(cudaMalloc(&ctx->d_one, sizeof(int)));
+  CKB(cudaMalloc(&ctx->d_err, sizeof(unsigned)));
+  CKB(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+  const int one = 1;
+  CKB(cudaMemcpy(ctx->d_one, &one, sizeof(int), cudaMemcpyHostToDevice));
+  Desc &d = *ctx->h_desc;
+  memset(&d, 0, sizeof(Desc));
+  d.N = N; d.bc = bc; d.prec = prec;
+  d.pitch_s = ctx->pitch_s; d.pitch_g = ctx->pitch_g;
+  d.plane_s = ctx->plane_s; d.plane_g = ctx->plane_g;
+  d.inv_h2 = 1.0 / (ctx->h * ctx->h);
+  d.mu2 = mu * mu;
+  d.lambda = lambda;
+  d.t0 = 0.0; d.dt = 0.0;
+  d.n_base = 0; d.n_end = 0; d.stop_k = kNoStop; d.stop_thr = 0.0;
+  d.maxabs = ctx->d_maxabs;
+  d.tmaps = ctx->d_tmaps;
+  for (int i = 0; i < NUM_FIELDS; ++i) d.f[i] = ctx->f[i];
+  if ((st = push_desc(ctx)) != HBE_OK) return bail(st);
+  if ((st = apply_tuning(ctx, 0, 0)) != HBE_OK) return bail(st);
+  *out = ctx;
+  return HBE_OK;
+#undef CKB
+}
+
+}  // namespace
+
+// =============================================================== C ABI
+extern "C" {
+
+const char *hbe_status_string(int s) {
+  static const char *names[] = {"HBE_OK", "HBE_EINVAL", "HBE_ENOMEM", "HBE_ECUDA",
+                                "HBE_ESTATE", "HBE_STOPPED", "HBE_NONFINITE", "HBE_ETIMEOUT"};
+  return (s >= 0 && s <= 7) ? names[s] : "unknown";
+}
+
+hbe_status hbe_workspace_bytes(int N, int bc, int prec, size_t *bytes) {
+  std::string e;
+  if (!bytes) return HBE_EINVAL;
+  hbe_status st = validate(e, N, 1.0, 0.0, 0.0, bc, prec);
+  if (st != HBE_OK) return st;
+  *bytes = workspace_bytes(N, prec);
+  return HBE_OK;
+}
+
+hbe_status hbe_create(int N, double L, double mu, double lambda, int bc, int prec, hbe_ctx **out) {
+  return create_common(N, L, mu, lambda, bc, prec, nullptr, 0, out);
+}
+
+hbe_status hbe_create_in(int N, double L, double mu, double lambda, int bc, int prec,
+                         void *d_workspace, size_t bytes, hbe_ctx **out) {
+  if (!d_workspace) return HBE_EINVAL;
+  return create_common(N, L, mu, lambda, bc, prec, d_workspace, bytes, out);
+}
+
+void hbe_destroy(hbe_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->stream || ctx->cap_stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
+  cudaFree(ctx->d_tmaps);
+  cudaFree(ctx->d_maxabs);
+  cudaFree(ctx->d_desc);
+  if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
+  cudaFree(ctx->d_items);
+  cudaFree(ctx->d_nitems);
+  cudaFree(ctx->d_one);
+  cudaFree(ctx->d_err);
+  cudaFree(ctx->d_stage);
+  cudaFree(ctx->d_masks);
+  cudaFree(ctx->d_labels);
+  cudaFree(ctx->d_counts);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  delete ctx;
+}
+
+hbe_status hbe_set_stream(hbe_ctx *ctx, void *stream) {
+  if (!ctx) return HBE_EINVAL;
+  if (ctx->pending) {
+    hbe_status st = sync_ctx(ctx);
+    if (st != HBE_OK) return st;
+  }
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return HBE_OK;
+}
+
+int hbe_variant_count(int prec) {
+  if (prec < HBE_FP64 || prec > HBE_FP32_PLAIN) return 0;
+  return table_for(prec).count;
+}
+
+hbe_status hbe_variant_info(int prec, int variant, hbe_variant_t *out) {
+  if (!out || prec < HBE_FP64 || prec > HBE_FP32_PLAIN) return HBE_EINVAL;
+  const VariantTable &vt = table_for(prec);
+  if (variant < 0 || variant >= vt.count) return HBE_EINVAL;
+  const KernelInfo *k = vt.k[variant];
+  out->tile_x = k[0].tx;
+  out->tile_y = k[0].ty;
+  out->threads = k[0].threads;
+  for (int s = 0; s < 4; ++s) {
+    out->smem_bytes[s] = k[s].smem;
+    out->ring[s] = k[s].ring;
+  }
+  return HBE_OK;
+}
+
+hbe_status hbe_set_tuning(hbe_ctx *ctx, int variant, int zchunk) {
+  if (!ctx) return HBE_EINVAL;
+  if (ctx->in_batch) return set_err(ctx->err, HBE_ESTATE, "context is in a batch");
+  if (ctx->pending) {
+    hbe_status st = sync_ctx(ctx);
+    if (st != HBE_OK) return st;
+  }
+  return apply_tuning(ctx, variant, zchunk);
+}
+
+static hbe_status set_initial_impl(hbe_ctx *ctx, const double *phi0, const double *phi1, double t0,
+                                   bool device) {
+  if (!ctx || !phi0 || !phi1) return HBE_EINVAL;
+  if (ctx->in_batch) return set_err(ctx->err, HBE_ESTATE, "context is in a batch");
+  if (!std::isfinite(t0)) return set_err(ctx->err, HBE_EINVAL, "t0 must be finite");
+  hbe_status st = sync_ctx(ctx);
+  if (st != HBE_OK) return st;
+  const int N = ctx->N;
+  const int sprec = ctx->prec == HBE_FP64 ? 0 : 1;
+  const bool kahan = is_kahan(ctx->prec);
+  const size_t plane = (size_t)N * N;
+  if (device) {
+    CK(launch_pack(sprec, phi0, ctx->f[F_P0], kahan ? ctx->f[F_PLO0] : nullptr, N, ctx->pitch_s,
+                   ctx->hxs, ctx->bc, 0, N, ctx->stream));
+    CK(launch_pack(sprec, phi1, ctx->f[F_Q0], kahan ? ctx->f[F_QLO0] : nullptr, N, ctx->pitch_s,
+                   ctx->hxs, ctx->bc, 0, N, ctx->stream));
+  } else {
+    if ((st = ensure_stage_buffer(ctx)) != HBE_OK) return st;
+    const int zs = (int)(ctx->stage_elems / plane);
+    double *s0 = ctx->d_stage, *s1 = ctx->d_stage + ctx->stage_elems;
+    for (int z = 0; z < N; z += zs) {
+      const int nz = std::min(zs, N - z);
+      CK(cudaMemcpyAsync(s0, phi0 + (size_t)z * plane, nz * plane * sizeof(double),
+                         cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(s1, phi1 + (size_t)z * plane, nz * plane * sizeof(double),
+                         cudaMemcpyHostToDevice, ctx->stream));
+      CK(launch_pack(sprec, s0, ctx->f[F_P0],
+                     kahan ? ctx->f[F_PLO0] : nullptr, N, ctx->pitch_s, ctx->hxs, ctx->bc, z, nz,
+                     ctx->stream));
+      CK(launch_pack(sprec, s1, ctx->f[F_Q0], kahan ? ctx->f[F_QLO0] : nullptr, N, ctx->pitch_s,
+                     ctx->hxs, ctx->bc, z, nz, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
+  }
+  Desc &d = *ctx->h_desc;
+  d.t0 = t0;
+  d.dt = 0.0;
+  d.n_base = 0;
+  d.n_end = 0;
+  d.stop_k = kNoStop;
+  d.status = ST_RUNNING;
+  d.last_done = 0;
+  if ((st = push_desc(ctx)) != HBE_OK) return st;
+  CK(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+  ctx->has_state = true;
+  return HBE_OK;
+}
+
+hbe_status hbe_set_initial(hbe_ctx *ctx, const double *phi0, const double *phi1, double t0) {
+  return set_initial_impl(ctx, phi0, phi1, t0, false);
+}
+
+hbe_status hbe_set_initial_device(hbe_ctx *ctx, const double *d_phi0, const double *d_phi1,
+                                  double t0) {
+  hbe_status st = set_initial_impl(ctx, d_phi0, d_phi1, t0, true);
+  if (st == HBE_OK && ctx) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return set_err(ctx->err, HBE_ECUDA, "%s", cudaGetErrorString(e));
+  }
+  return st;
+}
+
+hbe_status hbe_set_stop(hbe_ctx *ctx, double threshold) {
+  if (!ctx) return HBE_EINVAL;
+  if (!(threshold >= 0.0)) return set_err(ctx->err, HBE_EINVAL, "threshold must be >= 0");
+  if (ctx->pending) {
+    hbe_status st = sync_ctx(ctx);
+    if (st != HBE_OK) return st;
+  }
+  ctx->h_desc->stop_thr = threshold;
+  ctx->desc_stale = true;
+  return HBE_OK;
+}
+
+hbe_status hbe_step_async(hbe_ctx *ctx, int64_t nsteps, double dt) {
+  if (!ctx) return HBE_EINVAL;
+  if (ctx->in_batch) return set_err(ctx->err, HBE_ESTATE, "context is in a batch");
+  if (!ctx->has_state) return set_err(ctx->err, HBE_ESTATE, "no initial data");
+  if (nsteps < 0) return set_err(ctx->err, HBE_EINVAL, "nsteps < 0");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return set_err(ctx->err, HBE_EINVAL, "dt must be > 0");
+  if (nsteps == 0) return HBE_OK;
+  hbe_status st;
+  Desc &d = *ctx->h_desc;
+  if (ctx->pending && dt != d.dt) {
+    if ((st = sync_ctx(ctx)) != HBE_OK) return st;
+  }
+  if (ctx->desc_stale) {
+    if ((st = push_desc(ctx)) != HBE_OK) return st;
+  }
+  if ((st = ensure_graph(ctx)) != HBE_OK) return st;
+  if (!ctx->pending) {
+    // restart: clear the stop status; a new dt moves the time origin to the current t
+    if (dt != d.dt) {
+      const double t_now = d.dt > 0.0 ? current_t(ctx) : d.t0;
+      d.t0 = t_now - (double)d.n_base * dt;
+      d.dt = dt;
+    }
+    CK(launch_set_run(ctx->d_desc, nsteps, d.t0, d.dt, d.stop_thr, 1, ctx->stream));
+  } else {
+    CK(launch_set_run(ctx->d_desc, nsteps, d.t0, d.dt, d.stop_thr, 0, ctx->stream));
+  }
+  const int64_t runs = (nsteps + ctx->K - 1) / ctx->K;
+  for (int64_t r = 0; r < runs; ++r) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+  ctx->launches += runs * 4 * ctx->K;
+  ctx->pending = true;
+  return HBE_OK;
+}
+
+hbe_status hbe_sync(hbe_ctx *ctx) {
+  if (!ctx) return HBE_EINVAL;
+  const bool was_pending = ctx->pending;
+  hbe_status st = sync_ctx(ctx);
+  if (st != HBE_OK) return st;
+  if (was_pending) {
+    if (ctx->h_desc->status == ST_STOPPED)
+      return set_err(ctx->err, HBE_STOPPED, "max|phi| passed the stop threshold at step %lld",
+                     (long long)ctx->h_desc->n_base);
+    if (ctx->h_desc->status == ST_NONFINITE)
+      return set_err(ctx->err, HBE_NONFINITE, "phi became non-finite at step %lld",
+                     (long long)ctx->h_desc->n_base);
+  }
+  return HBE_OK;
+}
+
+hbe_status hbe_step(hbe_ctx *ctx, int64_t nsteps, double dt) {
+  hbe_status st = hbe_step_async(ctx, nsteps, dt);
+  if (st != HBE_OK) return st;
+  return hbe_sync(ctx);
+}
+
+hbe_status hbe_profile_stages(hbe_ctx *ctx, int64_t nsteps, double dt, float *ms_per_stage) {
+  if (!ctx || !ms_per_stage) return HBE_EINVAL;
+  if (ctx->in_batch) return set_err(ctx->err, HBE_ESTATE, "context is in a batch");
+  if (!ctx->has_state) return set_err(ctx->err, HBE_ESTATE, "no initial data");
+  if (nsteps < 1 || nsteps > 4096) return set_err(ctx->err, HBE_EINVAL, "nsteps in [1, 4096]");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return set_err(ctx->err, HBE_EINVAL, "dt must be > 0");
+  hbe_status st = sync_ctx(ctx);
+  if (st != HBE_OK) return st;
+  if (ctx->desc_stale && (st = push_desc(ctx)) != HBE_OK) return st;
+  Desc &d = *ctx->h_desc;
+  if (dt != d.dt) {
+    const double t_now = d.dt > 0.0 ? current_t(ctx) : d.t0;
+    d.t0 = t_now - (double)d.n_base * dt;
+    d.dt = dt;
+  }
+  CK(launch_set_run(ctx->d_desc, nsteps, d.t0, d.dt, d.stop_thr, 1, ctx->stream));
+  std::vector<cudaEvent_t> ev((size_t)nsteps * 5, nullptr);
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  const VariantTable &vt = table_for(ctx->prec);
+  for (int64_t n = 0; n < nsteps && st == HBE_OK; ++n) {
+    for (int s = 0; s < 4 && st == HBE_OK; ++s) {
+      CK(cudaEventRecord(ev[n * 5 + s], ctx->stream));
+      StageParams p{ctx->d_desc, ctx->d_items, ctx->d_nitems, ctx->d_err, 0};
+      st = launch_stage(ctx->err, vt.k[ctx->variant][s], ctx->grid[s], p, ctx->stream);
+    }
+    CK(cudaEventRecord(ev[n * 5 + 4], ctx->stream));
+    CK(launch_advance(ctx->d_desc, ctx->d_one, 1, 1, ctx->stream));
+  }
+  ctx->launches += nsteps * 4;
+  ctx->pending = true;
+  hbe_status st2 = sync_ctx(ctx);
+  double acc[4] = {0, 0, 0, 0};
+  if (st == HBE_OK && st2 == HBE_OK) {
+    for (int64_t n = 0; n < nsteps; ++n)
+      for (int s = 0; s < 4; ++s) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[n * 5 + s], ev[n * 5 + s + 1]);
+        acc[s] += ms;
+      }
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  if (st != HBE_OK) return st;
+  if (st2 != HBE_OK) return st2;
+  for (int s = 0; s < 4; ++s) ms_per_stage[s] = (float)(acc[s] / (double)nsteps);
+  if (d.status == ST_STOPPED) return HBE_STOPPED;
+  if (d.status == ST_NONFINITE) return HBE_NONFINITE;
+  return HBE_OK;
+}
+
+hbe_status hbe_progress(hbe_ctx *ctx, int64_t *steps, double *t) {
+  if (!ctx) return HBE_EINVAL;
+  hbe_status st = sync_ctx(ctx);
+  if (st != HBE_OK) return st;
+  if (steps) *steps = ctx->h_desc->n_base;
+  if (t) *t = current_t(ctx);
+  return HBE_OK;
+}
+
+static hbe_status read_impl(hbe_ctx *ctx, double *phi, double *psi, bool device) {
+  const int N = ctx->N;
+  const int sprec = ctx->prec == HBE_FP64 ? 0 : 1;
+  const bool kahan = is_kahan(ctx->prec);
+  const int set = (int)(ctx->h_desc->n_base & 1);
+  void *hp = ctx->f[F_P0 + set], *hq = ctx->f[F_Q0 + set];
+  void *lp = kahan ? ctx->f[F_PLO0 + set] : nullptr, *lq = kahan ? ctx->f[F_QLO0 + set] : nullptr;
+  if (device) {
+    if (phi) CK(launch_unpack(sprec, hp, lp, phi, N, ctx->pitch_s, ctx->hxs, 0, N, ctx->stream));
+    if (psi) CK(launch_unpack(sprec, hq, lq, psi, N, ctx->pitch_s, ctx->hxs, 0, N, ctx->stream));
+    return HBE_OK;
+  }
+  hbe_status st = ensure_stage_buffer(ctx);
+  if (st != HBE_OK) return st;
+  const size_t plane = (size_t)N * N;
+  const int zs = (int)(ctx->stage_elems / plane);
+  for (int z = 0; z < N; z += zs) {
+    const int nz = std::min(zs, N - z);
+    if (phi) {
+      CK(launch_unpack(sprec, hp, lp, ctx->d_stage, N, ctx->pitch_s, ctx->hxs, z, nz, ctx->stream));
+      CK(cudaMemcpyAsync(phi + (size_t)z * plane, ctx->d_stage, nz * plane * sizeof(double),
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    if (psi) {
+      CK(launch_unpack(sprec, hq, lq, ctx->d_stage + ctx->stage_elems, N, ctx->pitch_s, ctx->hxs, z,
+                       nz, ctx->stream));
+      CK(cudaMemcpyAsync(psi + (size_t)z * plane, ctx->d_stage + ctx->stage_elems,
+                         nz * plane * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return HBE_OK;
+}
+
+hbe_status hbe_read(hbe_ctx *ctx, double *phi, double *psi, double *t) {
+  if (!ctx) return HBE_EINVAL;
+  if (!ctx->has_state) return set_err(ctx->err, HBE_ESTATE, "no initial data");
+  hbe_status st = sync_ctx(ctx);
+  if (st != HBE_OK) return st;
+  if (t) *t = current_t(ctx);
+  if (!phi && !psi) return HBE_OK;
+  return read_impl(ctx, phi, psi, false);
+}
+
+hbe_status hbe_read_device(hbe_ctx *ctx, double *d_phi, double *d_psi) {
+  if (!ctx) return HBE_EINVAL;
+  if (!ctx->has_state) return set_err(ctx->err, HBE_ESTATE, "no initial data");
+  hbe_status st = sync_ctx(ctx);
+  if (st != HBE_OK) return st;
+  return read_impl(ctx, d_phi, d_psi, true);
+}
+
+hbe_status hbe_diag(hbe_ctx *ctx, double eps, hbe_diag_t *out, uint32_t *pos_mask,
+                    uint32_t *neg_mask) {
+  if (!ctx || !out) return HBE_EINVAL;
+  if (!ctx->has_state) return set_err(ctx->err, HBE_ESTATE, "no initial data");
+  if (!(eps >= 0.0)) return set_err(ctx->err, HBE_EINVAL, "eps must be >= 0");
+  if ((int64_t)ctx->N * ctx->N * ctx->N >= 0x7fffffffLL)
+    return set_err(ctx->err, HBE_EINVAL, "diagnostics need N^3 < 2^31");
+  hbe_status st = sync_ctx(ctx);
+  if (st != HBE_OK) return st;
+  const int N = ctx->N;
+  const size_t words = (size_t)N * N * ((N + 31) / 32);
+  if (!ctx->d_masks) {
+    CK(cudaMalloc(&ctx->d_masks, 2 * words * sizeof(uint32_t)));
+    CK(cudaMalloc(&ctx->d_labels, (size_t)N * N * N * sizeof(int)));
+    CK(cudaMalloc(&ctx->d_counts, 4 * sizeof(unsigned long long)));
+  }
+  const int sprec = ctx->prec == HBE_FP64 ? 0 : 1;
+  const bool kahan = is_kahan(ctx->prec);
+  const int set = (int)(ctx->h_desc->n_base & 1);
+  CK(cudaMemsetAsync(ctx->d_counts, 0, 4 * sizeof(unsigned long long), ctx->stream));
+  CK(launch_signpack(sprec, ctx->f[F_P0 + set], kahan ? ctx->f[F_PLO0 + set] : nullptr, N,
+                     ctx->pitch_s, ctx->hxs, eps, ctx->d_masks, ctx->d_masks + words,
+                     ctx->d_counts, ctx->stream));
+  CK(launch_ccl(ctx->d_masks, N, ctx->bc, ctx->d_labels, ctx->d_counts + 1, ctx->d_err, ctx->stream));
+  CK(launch_ccl(ctx->d_masks + words, N, ctx->bc, ctx->d_labels, ctx->d_counts + 2, ctx->d_err,
+                ctx->stream));
+  unsigned long long c[4];
+  CK(cudaMemcpyAsync(c, ctx->d_counts, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream));
+  if (pos_mask)
+    CK(cudaMemcpyAsync(pos_mask, ctx->d_masks, words * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  if (neg_mask)
+    CK(cudaMemcpyAsync(neg_mask, ctx->d_masks + words, words * sizeof(uint32_t),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+  if ((st = sync_ctx(ctx)) != HBE_OK) return st;
+  double mx;
+  memcpy(&mx, &c[0], sizeof(double));
+  out->t = current_t(ctx);
+  out->step = ctx->h_desc->n_base;
+  out->finite = std::isfinite(mx) ? 1 : 0;
+  out->max_abs_phi = mx;
+  out->reserved = 0;
+  out->n_pos = (int64_t)c[1];
+  out->n_neg = (int64_t)c[2];
+  const int64_t b = out->n_pos + out->n_neg - 1;
+  out->bubble_count = b > 0 ? b : 0;
+  return HBE_OK;
+}
+
+namespace {
+struct SaveHeader {
+  char magic[8];
+  int32_t N, bc, prec, pad;
+  double L, mu, lambda, t0, dt, stop_thr;
+  int64_t n_base;
+  uint64_t field_bytes;
+};
+}  // namespace
+
+hbe_status hbe_save(hbe_ctx *ctx, const char *path) {
+  if (!ctx || !path) return HBE_EINVAL;
+  if (!ctx->has_state) return set_err(ctx->err, HBE_ESTATE, "no initial data");
+  hbe_status st = sync_ctx(ctx);
+  if (st != HBE_OK) return st;
+  FILE *fp = fopen(path, "wb");
+  if (!fp) return set_err(ctx->err, HBE_EINVAL, "cannot open %s", path);
+  SaveHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  memcpy(hd.magic, "HBESAVE1", 8);
+  const Desc &d = *ctx->h_desc;
+  hd.N = ctx->N; hd.bc = ctx->bc; hd.prec = ctx->prec;
+  hd.L = ctx->L; hd.mu = ctx->mu; hd.lambda = ctx->lambda;
+  hd.t0 = d.t0; hd.dt = d.dt; hd.stop_thr = d.stop_thr; hd.n_base = d.n_base;
+  hd.field_bytes = ctx->bytes_s;
+  bool ok = fwrite(&hd, sizeof(hd), 1, fp) == 1;
+  const int set = (int)(d.n_base & 1);
+  const int nf = is_kahan(ctx->prec) ? 4 : 2;
+  const int fields[4] = {F_P0 + set, F_Q0 + set, F_PLO0 + set, F_QLO0 + set};
+  std::vector<char> buf(ctx->bytes_s);
+  for (int i = 0; i < nf && ok; ++i) {
+    if (cudaMemcpy(buf.data(), ctx->f[fields[i]], ctx->bytes_s, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      fclose(fp);
+      return set_err(ctx->err, HBE_ECUDA, "device read failed");
+    }
+    ok = fwrite(buf.data(), 1, ctx->bytes_s, fp) == ctx->bytes_s;
+  }
+  fclose(fp);
+  return ok ? HBE_OK : set_err(ctx->err, HBE_EINVAL, "write to %s failed", path);
+}
+
+hbe_status hbe_load(hbe_ctx *ctx, const char *path) {
+  if (!ctx || !path) return HBE_EINVAL;
+  if (ctx->in_batch) return set_err(ctx->err, HBE_ESTATE, "context is in a batch");
+  hbe_status st = sync_ctx(ctx);
+  if (st != HBE_OK) return st;
+  FILE *fp = fopen(path, "rb");
+  if (!fp) return set_err(ctx->err, HBE_EINVAL, "cannot open %s", path);
+  SaveHeader hd;
+  if (fread(&hd, sizeof(hd), 1, fp) != 1 || memcmp(hd.magic, "HBESAVE1", 8) != 0 ||
+      hd.N != ctx->N || hd.bc != ctx->bc || hd.prec != ctx->prec ||
+      hd.field_bytes != ctx->bytes_s) {
+    fclose(fp);
+    return set_err(ctx->err, HBE_EINVAL, "%s is not a checkpoint of this problem shape", path);
+  }
+  const int set = (int)(hd.n_base & 1);
+  const int nf = is_kahan(ctx->prec) ? 4 : 2;
+  const int fields[4] = {F_P0 + set, F_Q0 + set, F_PLO0 + set, F_QLO0 + set};
+  std::vector<char> buf(ctx->bytes_s);
+  for (int i = 0; i < nf; ++i) {
+    if (fread(buf.data(), 1, ctx->bytes_s, fp) != ctx->bytes_s) {
+      fclose(fp);
+      return set_err(ctx->err, HBE_EINVAL, "%s is truncated", path);
+    }
+    CK(cudaMemcpy(ctx->f[fields[i]], buf.data(), ctx->bytes_s, cudaMemcpyHostToDevice));
+  }
+  fclose(fp);
+  Desc &d = *ctx->h_desc;
+  d.t0 = hd.t0; d.dt = hd.dt; d.stop_thr = hd.stop_thr;
+  d.n_base = hd.n_base; d.n_end = hd.n_base; d.stop_k = kNoStop; d.status = ST_RUNNING;
+  if ((st = push_desc(ctx)) != HBE_OK) return st;
+  ctx->has_state = true;
+  return HBE_OK;
+}
+
+const char *hbe_last_error(const hbe_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t hbe_launch_count(const hbe_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+// =============================================================== batches
+hbe_status hbe_batch_create(int prec, int K, void *stream, hbe_batch **out) {
+  if (!out || prec < HBE_FP64 || prec > HBE_FP32_PLAIN || K < 1 || K > kMaxK) return HBE_EINVAL;
+  *out = nullptr;
+  hbe_batch *b = new hbe_batch();
+  b->prec = prec;
+  b->K = K;
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->nvariants = table_for(prec).count;
+  std::string e;
+  if (get_encoder(e) != HBE_OK || cudaGetDevice(&b->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&b->d_err, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(b->d_err, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&b->d_ndesc, sizeof(int)) != cudaSuccess) {
+    hbe_batch_destroy(b);
+    return HBE_ECUDA;
+  }
+  *out = b;
+  return HBE_OK;
+}
+
+void hbe_batch_destroy(hbe_batch *b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  for (hbe_ctx *c : b->members) c->in_batch = false;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  cudaFree(b->d_descs);
+  if (b->h_descs) cudaFreeHost(b->h_descs);
+  cudaFree(b->d_ndesc);
+  for (auto &l : b->lists) {
+    cudaFree(l.d_items);
+    cudaFree(l.d_n);
+  }
+  cudaFree(b->d_err);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+int hbe_batch_size(const hbe_batch *b) { return b ? (int)b->members.size() : 0; }
+const char *hbe_batch_last_error(const hbe_batch *b) { return b ? b->err.c_str() : "null batch"; }
+int64_t hbe_batch_launch_count(const hbe_batch *b) { return b ? b->launches : 0; }
+
+hbe_status hbe_batch_add(hbe_batch *b, hbe_ctx *ctx, int64_t nsteps, double dt) {
+  if (!b || !ctx) return HBE_EINVAL;
+  if (ctx->prec != b->prec) return set_err(b->err, HBE_EINVAL, "precision differs from the batch");
+  if (ctx->in_batch) return set_err(b->err, HBE_ESTATE, "context already in a batch");
+  if (!ctx->has_state) return set_err(b->err, HBE_ESTATE, "context has no initial data");
+  if (nsteps < 0 || !(dt > 0.0)) return set_err(b->err, HBE_EINVAL, "bad nsteps/dt");
+  hbe_status st = sync_ctx(ctx);
+  if (st != HBE_OK) return set_err(b->err, st, "%s", ctx->err.c_str());
+  Desc &d = *ctx->h_desc;
+  if (dt != d.dt) {
+    const double t_now = d.dt > 0.0 ? current_t(ctx) : d.t0;
+    d.t0 = t_now - (double)d.n_base * dt;
+    d.dt = dt;
+  }
+  d.n_end = d.n_base + nsteps;
+  d.stop_k = kNoStop;
+  d.status = ST_RUNNING;
+  ctx->in_batch = true;
+  b->members.push_back(ctx);
+  b->dirty = true;
+  return HBE_OK;
+}
+
+static void leave_batch(hbe_ctx *ctx) {
+  ctx->in_batch = false;
+  ctx->desc_stale = true;  // the member's own descriptor copy is older than the mirror
+}
+
+hbe_status hbe_batch_remove(hbe_batch *b, hbe_ctx *ctx) {
+  if (!b || !ctx) return HBE_EINVAL;
+  auto it = std::find(b->members.begin(), b->members.end(), ctx);
+  if (it == b->members.end()) return set_err(b->err, HBE_EINVAL, "not a member");
+  cudaStreamSynchronize(b->stream);
+  b->members.erase(it);
+  leave_batch(ctx);
+  b->dirty = true;
+  return HBE_OK;
+}
+
+static hbe_status batch_rebuild(hbe_batch *b) {
+  const int M = (int)b->members.size();
+  bool recapture = !b->gexec;
+  if (M > b->cap_desc) {
+    int cap = std::max(64, b->cap_desc);
+    while (cap < M) cap *= 2;
+    cudaFree(b->d_descs);
+    if (b->h_descs) cudaFreeHost(b->h_descs);
+    b->d_descs = nullptr;
+    b->h_descs = nullptr;
+    CKX(b->err, cudaMalloc(&b->d_descs, cap * sizeof(Desc)));
+    CKX(b->err, cudaMallocHost(&b->h_descs, cap * sizeof(Desc)));
+    b->cap_desc = cap;
+    recapture = true;
+  }
+  std::vector<WorkItem> items[kMaxVariants];
+  for (int i = 0; i < M; ++i) {
+    hbe_ctx *c = b->members[i];
+    b->h_descs[i] = *c->h_desc;
+    build_items(c, i, c->zchunk, items[c->variant]);
+  }
+  const VariantTable &vt = table_for(b->prec);
+  for (int v = 0; v < b->nvariants; ++v) {
+    auto &l = b->lists[v];
+    const int n = (int)items[v].size();
+    if (n > l.cap || !l.d_n) {
+      int cap = std::max(4096, l.cap);
+      while (cap < n) cap *= 2;
+      cudaFree(l.d_items);
+      l.d_items = nullptr;
+      if (!l.d_n) CKX(b->err, cudaMalloc(&l.d_n, sizeof(int)));
+      CKX(b->err, cudaMalloc(&l.d_items, cap * sizeof(WorkItem)));
+      l.cap = cap;
+      for (int s = 0; s < 4; ++s) {
+        hbe_status st = persistent_grid(b->err, vt.k[v][s], b->sms, &l.grid[s]);
+        if (st != HBE_OK) return st;
+      }
+      recapture = true;
+    }
+    if (n)
+      CKX(b->err, cudaMemcpyAsync(l.d_items, items[v].data(), n * sizeof(WorkItem),
+                                  cudaMemcpyHostToDevice, b->stream));
+    CKX(b->err, cudaMemcpyAsync(l.d_n, &n, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    CKX(b->err, cudaStreamSynchronize(b->stream));  // n lives on this stack frame
+  }
+  CKX(b->err, cudaMemcpyAsync(b->d_descs, b->h_descs, M * sizeof(Desc), cudaMemcpyHostToDevice,
+                              b->stream));
+  CKX(b->err, cudaMemcpyAsync(b->d_ndesc, &M, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  CKX(b->err, cudaStreamSynchronize(b->stream));
+  if (recapture) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    cudaGraph_t g = nullptr;
+    CKX(b->err, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    hbe_status st = HBE_OK;
+    for (int k = 0; k < b->K && st == HBE_OK; ++k)
+      for (int s = 0; s < 4 && st == HBE_OK; ++s)
+        for (int v = 0; v < b->nvariants && st == HBE_OK; ++v) {
+          auto &l = b->lists[v];
+          if (!l.d_n) continue;
+          StageParams p{b->d_descs, l.d_items, l.d_n, b->d_err, k};
+          st = launch_stage(b->err, vt.k[v][s], l.grid[s], p, b->cap_stream);
+        }
+    cudaError_t e = launch_advance(b->d_descs, b->d_ndesc, b->cap_desc, b->K, b->cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+    if (st != HBE_OK) return st;
+    CKX(b->err, e);
+    CKX(b->err, e2);
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    CKX(b->err, e);
+  }
+  b->dirty = false;
+  return HBE_OK;
+}
+
+hbe_status hbe_batch_run(hbe_batch *b, hbe_ctx **finished, int max_finished, int *n_finished) {
+  if (!b || !n_finished) return HBE_EINVAL;
+  *n_finished = 0;
+  if (b->members.empty()) return HBE_OK;
+  if (b->dirty) {
+    hbe_status st = batch_rebuild(b);
+    if (st != HBE_OK) return st;
+  }
+  const int M = (int)b->members.size();
+  CKX(b->err, cudaGraphLaunch(b->gexec, b->stream));
+  int used = 0;
+  for (int v = 0; v < b->nvariants; ++v) used += b->lists[v].d_n ? 1 : 0;
+  b->launches += (int64_t)4 * b->K * used;
+  CKX(b->err, cudaMemcpyAsync(b->h_descs, b->d_descs, M * sizeof(Desc), cudaMemcpyDeviceToHost,
+                              b->stream));
+  CKX(b->err, cudaStreamSynchronize(b->stream));
+  unsigned e = 0;
+  CKX(b->err, cudaMemcpy(&e, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (e) return set_err(b->err, HBE_ETIMEOUT, "a stage kernel's TMA wait timed out");
+  std::vector<hbe_ctx *> keep;
+  for (int i = 0; i < M; ++i) {
+    hbe_ctx *c = b->members[i];
+    *c->h_desc = b->h_descs[i];
+    c->launches += (int64_t)4 * b->K;
+    const Desc &d = b->h_descs[i];
+    if (d.n_base >= d.n_end || d.status != ST_RUNNING) {
+      leave_batch(c);
+      if (*n_finished < max_finished && finished) finished[*n_finished] = c;
+      ++*n_finished;
+      b->dirty = true;
+    } else {
+      keep.push_back(c);
+    }
+  }
+  b->members.swap(keep);
+  return HBE_OK;
+}
+
+}  // extern "C"

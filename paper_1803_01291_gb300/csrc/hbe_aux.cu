@@ -1,0 +1,284 @@
+// hbe_aux.cu -- kernels around the stage kernels: field packing, per-batch
+// step bookkeeping, and the diagnostics of Sec. 1 / Sec. 3 (max|phi|, sign
+// masks, connected components of the sign sets = bubbles).
+#include <cuda_bf16.h>
+
+#include "hbe_aux.h"
+
+namespace hbe {
+
+// ---------------------------------------------------------------- packing
+// Dense N^3 doubles -> padded field (hi, and lo = residual when lo != nullptr).
+// Every padded position is written: interior, periodic ghost copies (edge
+// ghosts only; the star stencil never reads corners), zeros elsewhere.
+template <class T>
+__global__ void pack_kernel(const double *__restrict__ src, T *__restrict__ hi,
+                            T *__restrict__ lo, int N, int pitch, int hx, int periodic,
+                            int z_begin, int z_count) {
+  const int64_t plane = (int64_t)(N + 4) * pitch;
+  const int64_t total = plane * z_count;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int zl = (int)(i / plane);
+    const int64_t r = i - (int64_t)zl * plane;
+    const int yp = (int)(r / pitch), xp = (int)(r - (int64_t)yp * pitch);
+    int x = xp - hx, y = yp - 2;
+    const bool xin = x >= 0 && x < N, yin = y >= 0 && y < N;
+    double v = 0.0;
+    bool have = false;
+    if (xin && yin) {
+      have = true;
+    } else if (periodic) {
+      if (yin && x >= -2 && x < N + 2) { x = (x + N) % N; have = true; }
+      else if (xin && y >= -2 && y < N + 2) { y = (y + N) % N; have = true; }
+    }
+    if (have) v = src[((int64_t)zl * N + y) * N + x];
+    const int64_t o = (int64_t)(z_begin + zl) * plane + r;
+    const T h = (T)v;
+    hi[o] = h;
+    if (lo) lo[o] = (T)(v - (double)h);
+  }
+}
+
+template <class T>
+__global__ void unpack_kernel(const T *__restrict__ hi, const T *__restrict__ lo,
+                              double *__restrict__ dst, int N, int pitch, int hx, int z_begin,
+                              int z_count) {
+  const int64_t plane = (int64_t)(N + 4) * pitch;
+  const int64_t total = (int64_t)N * N * z_count;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int zl = (int)(i / ((int64_t)N * N));
+    const int64_t r = i - (int64_t)zl * N * N;
+    const int y = (int)(r / N), x = (int)(r - (int64_t)y * N);
+    const int64_t o = (int64_t)(z_begin + zl) * plane + (int64_t)(y + 2) * pitch + x + hx;
+    double v = (double)hi[o];
+    if (lo) v += (double)lo[o];
+    dst[i] = v;
+  }
+}
+
+static int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_pack(int prec, const double *src, void *hi, void *lo, int N, int pitch, int hx,
+                        int periodic, int z_begin, int z_count, cudaStream_t st) {
+  const int64_t n = (int64_t)(N + 4) * pitch * z_count;
+  if (prec == 0) {
+    pack_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
+        src, (double *)hi, (double *)lo, N, pitch, hx, periodic, z_begin, z_count);
+  } else {
+    pack_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(
+        src, (float *)hi, (float *)lo, N, pitch, hx, periodic, z_begin, z_count);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(int prec, const void *hi, const void *lo, double *dst, int N, int pitch,
+                          int hx, int z_begin, int z_count, cudaStream_t st) {
+  const int64_t n = (int64_t)N * N * z_count;
+  if (prec == 0) {
+    unpack_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
+        (const double *)hi, (const double *)lo, dst, N, pitch, hx, z_begin, z_count);
+  } else {
+    unpack_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(
+        (const float *)hi, (const float *)lo, dst, N, pitch, hx, z_begin, z_count);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- bookkeeping
+// After K steps of a batch: count the steps each context executed, apply the
+// stop rule to the last of them, advance n_base, and clear the per-step maxima.
+__global__ void advance_kernel(Desc *descs, const int *ndesc, int K) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *ndesc) return;
+  Desc &d = descs[i];
+  long long exec = K;
+  if (d.n_end - d.n_base < exec) exec = d.n_end - d.n_base;
+  if (d.stop_k < exec) exec = d.stop_k;
+  if (exec < 0) exec = 0;
+  int status = ST_RUNNING;
+  if (exec > 0) {
+    const double m = __longlong_as_double((long long)d.maxabs[exec - 1]);
+    if (!(m <= 1.7976931348623157e308)) status = ST_NONFINITE;
+    else if (d.stop_thr > 0.0 && m > d.stop_thr) status = ST_STOPPED;
+  }
+  d.n_base += exec;
+  d.last_done = exec;
+  if (status != ST_RUNNING) {
+    d.status = status;
+    d.n_end = d.n_base;  // nothing more until the host asks again
+  }
+  d.stop_k = kNoStop;
+  for (int k = 0; k < K; ++k) d.maxabs[k] = 0ull;
+}
+
+cudaError_t launch_advance(Desc *descs, const int *ndesc, int max_desc, int K, cudaStream_t st) {
+  const int threads = 128;
+  advance_kernel<<<(max_desc + threads - 1) / threads, threads, 0, st>>>(descs, ndesc, K);
+  return cudaGetLastError();
+}
+
+// Host-requested changes to a running context, applied in stream order.
+__global__ void set_run_kernel(Desc *d, long long add_steps, double t0, double dt, double thr,
+                               int reset) {
+  if (reset) {
+    d->n_end = d->n_base;
+    d->status = ST_RUNNING;
+    d->stop_k = kNoStop;
+    d->t0 = t0;
+    d->dt = dt;
+    d->stop_thr = thr;
+  }
+  d->n_end += add_steps;
+}
+
+cudaError_t launch_set_run(Desc *d, long long add_steps, double t0, double dt, double thr,
+                           int reset, cudaStream_t st) {
+  set_run_kernel<<<1, 1, 0, st>>>(d, add_steps, t0, dt, thr, reset);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- diagnostics
+template <class T>
+__device__ __forceinline__ double state_at(const T *hi, const T *lo, int64_t o) {
+  double v = (double)hi[o];
+  if (lo) v += (double)lo[o];
+  return v;
+}
+
+// One warp per (y, z, word): bit x%32 of word x/32 of the two masks, plus the
+// running max of |phi| (NaN and inf read as +inf) as a double bit pattern.
+template <class T>
+__global__ void signpack_kernel(const T *__restrict__ hi, const T *__restrict__ lo, int N,
+                                int pitch, int hx, double eps, uint32_t *__restrict__ pos,
+                                uint32_t *__restrict__ neg, unsigned long long *maxbits) {
+  const int W = (N + 31) / 32;
+  const int64_t nwords = (int64_t)N * N * W;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t plane = (int64_t)(N + 4) * pitch;
+  double mx = 0.0;
+  for (int64_t wi = warp0; wi < nwords; wi += nwarps) {
+    const int64_t row = wi / W;
+    const int wx = (int)(wi - row * W);
+    const int z = (int)(row / N), y = (int)(row - (int64_t)z * N);
+    const int x = wx * 32 + lane;
+    double v = 0.0;
+    if (x < N) v = state_at(hi, lo, (int64_t)z * plane + (int64_t)(y + 2) * pitch + x + hx);
+    const unsigned bp = __ballot_sync(0xffffffffu, x < N && v > eps);
+    const unsigned bn = __ballot_sync(0xffffffffu, x < N && v < -eps);
+    if (lane == 0) { pos[wi] = bp; neg[wi] = bn; }
+    const double a = fabs(v);
+    mx = (a <= mx) ? mx : ((a == a) ? a : (double)INFINITY);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) atomicMax(maxbits, (unsigned long long)__double_as_longlong(mx));
+}
+
+__device__ __forceinline__ bool mask_bit(const uint32_t *m, int W, int N, int x, int y, int z) {
+  return (m[((int64_t)z * N + y) * W + (x >> 5)] >> (x & 31)) & 1u;
+}
+
+__device__ __forceinline__ int find_root(const int *L, int x) {
+  int y = __ldcg(L + x);
+  while (y != x) {
+    x = y;
+    y = __ldcg(L + x);
+  }
+  return x;
+}
+
+// Union of the sets of a and b: link the larger root under the smaller one
+// (labels only decrease, so every find terminates).  Bounded retries.
+__device__ __forceinline__ void unite(int *L, int a, int b, unsigned *err) {
+  for (int it = 0; it < (1 << 24); ++it) {
+    a = find_root(L, a);
+    b = find_root(L, b);
+    if (a == b) return;
+    if (a < b) {
+      const int old = atomicMin(L + b, a);
+      if (old == b) return;
+      b = old;
+    } else {
+      const int old = atomicMin(L + a, b);
+      if (old == a) return;
+      a = old;
+    }
+  }
+  atomicOr(err, (unsigned)DEV_ERR_UNIONFIND);
+}
+
+__global__ void ccl_init_kernel(const uint32_t *m, int N, int *L) {
+  const int W = (N + 31) / 32;
+  const int64_t n3 = (int64_t)N * N * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % N);
+    const int64_t r = i / N;
+    const int y = (int)(r % N), z = (int)(r / N);
+    L[i] = mask_bit(m, W, N, x, y, z) ? (int)i : -1;
+  }
+}
+
+// 6-connectivity: each set voxel joins its -x, -y, -z neighbours (and, when
+// periodic, the wrapped neighbour across the low face).
+__global__ void ccl_merge_kernel(const uint32_t *m, int N, int periodic, int *L, unsigned *err) {
+  const int W = (N + 31) / 32;
+  const int64_t n3 = (int64_t)N * N * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (__ldcg(L + i) < 0) continue;
+    const int x = (int)(i % N);
+    const int64_t r = i / N;
+    const int y = (int)(r % N), z = (int)(r / N);
+    const int xm = x > 0 ? x - 1 : (periodic ? N - 1 : -1);
+    const int ym = y > 0 ? y - 1 : (periodic ? N - 1 : -1);
+    const int zm = z > 0 ? z - 1 : (periodic ? N - 1 : -1);
+    if (xm >= 0 && mask_bit(m, W, N, xm, y, z)) unite(L, (int)i, (int)(((int64_t)z * N + y) * N + xm), err);
+    if (ym >= 0 && mask_bit(m, W, N, x, ym, z)) unite(L, (int)i, (int)(((int64_t)z * N + ym) * N + x), err);
+    if (zm >= 0 && mask_bit(m, W, N, x, y, zm)) unite(L, (int)i, (int)(((int64_t)zm * N + y) * N + x), err);
+  }
+}
+
+__global__ void ccl_count_kernel(const int *L, int64_t n3, unsigned long long *count) {
+  unsigned long long c = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3;
+       i += (int64_t)gridDim.x * blockDim.x)
+    c += (L[i] == (int)i) ? 1ull : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+cudaError_t launch_signpack(int prec, const void *hi, const void *lo, int N, int pitch, int hx,
+                            double eps, uint32_t *pos, uint32_t *neg, unsigned long long *maxbits,
+                            cudaStream_t st) {
+  const int64_t words = (int64_t)N * N * ((N + 31) / 32);
+  const int blocks = grid_for(words * 32, 256);
+  if (prec == 0)
+    signpack_kernel<double><<<blocks, 256, 0, st>>>((const double *)hi, (const double *)lo, N,
+                                                    pitch, hx, eps, pos, neg, maxbits);
+  else
+    signpack_kernel<float><<<blocks, 256, 0, st>>>((const float *)hi, (const float *)lo, N, pitch,
+                                                   hx, eps, pos, neg, maxbits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ccl(const uint32_t *mask, int N, int periodic, int *labels,
+                       unsigned long long *count, unsigned *err, cudaStream_t st) {
+  const int64_t n3 = (int64_t)N * N * N;
+  const int blocks = grid_for(n3, 256);
+  ccl_init_kernel<<<blocks, 256, 0, st>>>(mask, N, labels);
+  ccl_merge_kernel<<<blocks, 256, 0, st>>>(mask, N, periodic, labels, err);
+  ccl_count_kernel<<<blocks, 256, 0, st>>>(labels, n3, count);
+  return cudaGetLastError();
+}
+
+}  // namespace hbe

@@ -1,0 +1,21 @@
+// hbe_aux.h -- launchers of the non-stage kernels (hbe_aux.cu).
+#pragma once
+#include "hbe_common.cuh"
+
+namespace hbe {
+
+// prec here is the storage class of the state: 0 = double, 1 = float.
+cudaError_t launch_pack(int prec, const double *src, void *hi, void *lo, int N, int pitch, int hx,
+                        int periodic, int z_begin, int z_count, cudaStream_t st);
+cudaError_t launch_unpack(int prec, const void *hi, const void *lo, double *dst, int N, int pitch,
+                          int hx, int z_begin, int z_count, cudaStream_t st);
+cudaError_t launch_advance(Desc *descs, const int *ndesc, int max_desc, int K, cudaStream_t st);
+cudaError_t launch_set_run(Desc *d, long long add_steps, double t0, double dt, double thr,
+                           int reset, cudaStream_t st);
+cudaError_t launch_signpack(int prec, const void *hi, const void *lo, int N, int pitch, int hx,
+                            double eps, uint32_t *pos, uint32_t *neg, unsigned long long *maxbits,
+                            cudaStream_t st);
+cudaError_t launch_ccl(const uint32_t *mask, int N, int periodic, int *labels,
+                       unsigned long long *count, unsigned *err, cudaStream_t st);
+
+}  // namespace hbe

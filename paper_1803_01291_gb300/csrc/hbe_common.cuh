@@ -1,0 +1,74 @@
+// hbe_common.cuh -- types shared by the host side and the kernels of libhbe.
+//
+// Data layout in device memory (one per field, per precision):
+//   A field of N^3 unknowns is stored "padded": each x-row has HX ghost/alignment
+//   elements before and after it (HX = 16 bytes / element size, so the first
+//   unknown of a row is 16-byte aligned), each z-plane has 2 ghost rows before
+//   and after, and z is not padded:
+//       element (x, y, z) at  z*plane + (y + 2)*pitch + (x + HX),
+//       pitch = round_up(N + 2*HX, HX),  plane = (N + 4)*pitch.
+//   Zero-Dirichlet: ghosts stay 0 (the two ghost layers of Eq. BC, zeroed at
+//   allocation and never written).  Periodic: every writer also stores the
+//   wrapped copies x in {-2,-1,N,N+1} and y in {-2,-1,N,N+1}.  z-ghosts come
+//   from the TMA unit: out-of-range z planes read as zero (Dirichlet) or the
+//   plane index is wrapped (periodic).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hbe {
+
+enum Field : int {
+  F_P0 = 0, F_P1, F_Q0, F_Q1, F_PLO0, F_PLO1, F_QLO0, F_QLO1, F_G1, F_G2, F_G3, NUM_FIELDS
+};
+
+// TMA descriptors of one context: halo boxes (tile + 2 rows / HX columns of
+// ghost on each side) and interior boxes (the tile only).
+enum TMap : int {
+  TM_P_H0 = 0, TM_P_H1, TM_Q_H0, TM_Q_H1, TM_Q_I0, TM_Q_I1, TM_PLO_I0, TM_PLO_I1,
+  TM_QLO_I0, TM_QLO_I1, TM_G1_H, TM_G1_I, TM_G2_H, TM_G2_I, TM_G3_I, NUM_TMAPS
+};
+
+enum DevError : unsigned { DEV_ERR_TIMEOUT = 1u, DEV_ERR_UNIONFIND = 2u };
+
+enum StopStatus : int { ST_RUNNING = 0, ST_STOPPED = 1, ST_NONFINITE = 2 };
+
+constexpr long long kNoStop = 0x7fffffffffffffffLL;
+constexpr int kMaxK = 64;  // steps per captured graph
+
+// Per-context state the kernels read; host keeps a mirror.  All stage kernels
+// of one batch read it; only the per-batch advance kernel writes n_base,
+// n_end, stop_k and status (stage-1 kernels may lower stop_k).
+struct alignas(64) Desc {
+  int32_t N, bc, prec, pad0;
+  int32_t pitch_s, pitch_g;      // padded row pitch (elements) of state / G fields
+  int64_t plane_s, plane_g;      // elements per padded z-plane
+  double inv_h2, mu2, lambda;
+  double t0, dt;
+  int64_t n_base;                // steps completed before the current batch
+  int64_t n_end;                 // stop stepping when n reaches this
+  long long stop_k;              // first step index of the batch skipped by the stop rule
+  double stop_thr;               // 0: off
+  int64_t last_done;             // steps executed by the last batch (advance kernel)
+  int32_t status;                // StopStatus after the last batch
+  int32_t pad1;
+  unsigned long long *maxabs;    // [kMaxK] max|phi| after step k of the batch (double bits)
+  const CUtensorMap *tmaps;      // [NUM_TMAPS], 64-byte aligned, in device memory
+  void *f[NUM_FIELDS];
+};
+
+// Work item of a stage launch: one (context, x-y tile, z-chunk) column.
+// x = context index in the descriptor array, y = tile_x | tile_y << 16,
+// z = first plane, w = number of planes.
+using WorkItem = int4;
+
+struct StageParams {
+  Desc *descs;
+  const WorkItem *items;
+  const int *nitems;   // device scalar (the batch updates it between runs)
+  unsigned *err;       // device error word (DevError bits)
+  int k;               // step index within the batch
+};
+
+}  // namespace hbe

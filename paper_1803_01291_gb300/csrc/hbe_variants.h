@@ -1,0 +1,26 @@
+// hbe_variants.h -- tile variants of the stage kernels, per precision.
+#pragma once
+
+namespace hbe {
+
+struct KernelInfo {
+  const void *fn;   // __global__ stage_kernel<...>
+  int threads;
+  int smem;         // dynamic shared memory bytes
+  int ring;         // z-planes in the TMA ring
+  int tx, ty;       // tile in x and y
+};
+
+constexpr int kMaxVariants = 4;
+
+struct VariantTable {
+  int count;
+  KernelInfo k[kMaxVariants][4];  // [variant][stage-1]
+};
+
+const VariantTable &variants_fp64();
+const VariantTable &variants_fp32();
+const VariantTable &variants_bf16();
+const VariantTable &variants_fp32_plain();
+
+}  // namespace hbe
