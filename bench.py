@@ -1,0 +1,452 @@
+"""Throughput benchmark of the HBE RK4 + FD4 hot path on GB300.
+
+Workload: 512^3 unknowns on the periodic box [-20, 20]^3, mu = 1, lambda = 1,
+phi0 = seeded band-limited Gaussian random field (std 1, correlation length 2,
+seed 0), phi1 = 0, dt = T/nsteps <= h/4 (T = 6, 308 steps), FP32 fields with
+compensated (hi, lo) phi/psi and FP64 time/e^{-2t} coefficients.  One bench
+step = one full RK4 step (all four stage kernels) over the whole grid.
+
+Metric: Gpoint-steps/s = N^3 x steps / seconds (whole job: summed over ranks).
+The FP64, BF16-storage and plain-FP32 paths are measured on the same GPU and
+reported beside it.  The field state (>= 4 x 512 MiB) is larger than L2, so
+no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --impl reference the CPU oracle (plain FP64 C, all host cores) is timed
+on the same workload, each step one RK4 step on a 512 x 512 x 64 slab of it.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT = 512
+L_BOX = 40.0
+HORIZON = 6.0
+
+# algorithmic bytes per point of each stage kernel (reads + writes of the fields
+# a stage touches once each), per precision: (state bytes, G bytes, compensated)
+PREC_BYTES = {"fp64": (8, 8, False), "fp32": (4, 4, True), "bf16": (4, 2, True),
+              "fp32_plain": (4, 4, False)}
+
+
+def stage_bytes(prec: str):
+    s, g, comp = PREC_BYTES[prec]
+    b1 = 2 * s + g                 # p, q -> G1
+    b2 = 2 * s + 2 * g             # p, q, G1 -> G2
+    b3 = 2 * s + 3 * g             # p, q, G1, G2 -> G3
+    b4 = 2 * s + 3 * g + 2 * s     # p, q, G1, G2, G3 -> p', q'
+    if comp:
+        b4 += 4 * s                # lo parts of p and q, in and out
+    return [b1, b2, b3, b4]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 FMA rate of GB300 measured with a dependent-free FMA loop (0.58 TFMA/s,
+# 152 SMs, ~1.9 GHz): the FP64 stage kernels are bound by it, not by HBM.
+FP64_FMA_PER_S = 0.58e12
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for fn in ("hbe_stage.cuh", "hbe_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1803_01291_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(prec: str, N: int):
+    """dram bytes per launch of the stage-4 kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"stage4_{prec}_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        per_point = float(kv["dram_bytes_per_point"])
+    except (KeyError, ValueError):
+        return None
+    return per_point * N ** 3
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self._t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(gpus: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != gpus and world != 1:
+        raise SystemExit(f"--gpus {gpus} but WORLD_SIZE={world}")
+    return rank, world, local
+
+
+def barrier(world, torch):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value: float, world, torch, device):
+    if world == 1:
+        return value
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(N: int):
+    import hbe_inputs as hi
+    prob = hi.grf_problem(N, lam=1.0, seed=0)
+    return prob
+
+
+def time_path(hbe, torch, prob, prec_id, steps, warmup, profile_warm=True):
+    """Warm up, then time `steps` RK4 steps with the four stage kernels each
+    bracketed by CUDA events on the solver's stream.  Returns (seconds, per-stage ms)."""
+    s = hbe.Solver(prob.N, prob.L, prob.mu, prob.lam, prob.bc, prec_id)
+    phi0 = torch.from_numpy(prob.phi0).cuda()
+    phi1 = torch.from_numpy(prob.phi1).cuda()
+    s.set_initial(phi0, phi1)
+    del phi0, phi1
+    if warmup:
+        s.profile_stages(warmup, prob.dt)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    l0 = s.launches
+    e0.record(stream)
+    stage_ms = s.profile_stages(steps, prob.dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    # 4 stage kernels per step (counted by the library) + the per-step
+    # bookkeeping kernel + one run-setup kernel
+    launches = s.launches - l0 + steps + 1
+    s.close()
+    return secs, stage_ms, launches
+
+
+def e2e_solve(hbe, torch, prob, prec_id, nsteps):
+    """One solve through the public API with host buffers: initial data from
+    pinned host memory, nsteps on the GPU, phi back to pinned host memory."""
+    import numpy as np
+    N = prob.N
+    h0 = torch.from_numpy(prob.phi0).pin_memory()
+    h1 = torch.from_numpy(prob.phi1).pin_memory()
+    out = torch.empty((N, N, N), dtype=torch.float64).pin_memory()
+    s = hbe.Solver(N, prob.L, prob.mu, prob.lam, prob.bc, prec_id)
+    # warm (graph capture, staging buffers)
+    s.set_initial(h0.numpy(), h1.numpy())
+    s.step(2, prob.dt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_initial(h0.numpy(), h1.numpy())
+    st = s.step(nsteps, prob.dt)
+    import ctypes
+    tt = ctypes.c_double()
+    dp = ctypes.POINTER(ctypes.c_double)
+    s.lib.hbe_read(s.handle, ctypes.cast(out.data_ptr(), dp), None, ctypes.byref(tt))
+    secs = time.perf_counter() - t0
+    s.close()
+    return secs, st, float(np.abs(out.numpy()).max())
+
+
+def serve_leg(hbe, count: int = 256, seed: int = 0, load: float = 0.8):
+    """Continuous batching on the seeded stream of `count` solve requests
+    (N in {32..256}^3, mu, lambda ~ U[.5, 2], 1-4 bumps, T ~ U[1, 6], FP32 with
+    compensated state).  A closed-loop run measures the batched capacity; the
+    Poisson arrival rate is then set to `load` x capacity and the stream is
+    served in real time (p50/p99 latency = finish - arrival).  Baseline: the
+    same requests solved one after another, alone, on the FP64 path."""
+    import hbe_inputs as hi
+    from paper_1803_01291_gb300 import serve
+    stream = hi.request_stream(count, seed=seed, rate=1.0)
+    reqs = serve.requests_from_stream(stream)
+    total = sum(r.work for r in reqs)
+    srv = serve.Server(hbe.FP32, K=8)
+    cal = srv.run(reqs, realtime=False)
+    srv.close()
+    capacity = total / cal.makespan                  # point-steps / s
+    rate = load * capacity / (total / count)         # requests / s
+    for r in reqs:
+        r.arrival = r.arrival / rate                 # the stream was drawn at rate 1
+    srv = serve.Server(hbe.FP32, K=8)
+    live = srv.run(reqs, realtime=True)
+    srv.close()
+    alone = serve.run_alone(reqs, hbe.FP64)
+    out = live.summary()
+    out.update({"closed_loop_gpoint_steps_per_s": capacity / 1e9,
+                "arrival_rate_req_per_s": rate, "load": load,
+                "alone_fp64": alone,
+                "speedup_vs_alone_fp64": out["gpoint_steps_per_s"] / alone["gpoint_steps_per_s"],
+                "workload": f"{count} requests, seed {seed}, N in {{32,48,64,96,128,192,256}}^3, "
+                            "zero-Dirichlet [-10,10]^3, FP32 compensated, K = 8 steps per graph"})
+    return out
+
+
+def cpu_baseline(prob, nsteps=2):
+    """The oracle as it stands, on all host cores, nsteps RK4 steps of the full grid."""
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.run(prob.phi0, prob.phi1, prob.L, prob.mu, prob.lam, prob.bc, 0.0, prob.dt, nsteps,
+               nthreads=cores)
+    secs = time.perf_counter() - t0
+    pts = prob.N ** 3 * nsteps
+    return {"value": pts / secs / 1e9, "unit": "Gpoint-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{nsteps} RK4 steps of the full {prob.N}^3 workload (FP64 C oracle, "
+                      f"OpenMP over z, {cores} threads), {secs:.2f} s"}
+
+
+METRIC = "Gpoint-steps/s at 512^3 (FP32 vs FP64, same GB300); p50/p99 serve latency"
+
+
+def workload_config(N, prob, world=1):
+    return {"workload": "hbe-512-periodic-grf", "N": N, "L": L_BOX, "mu": 1.0, "lambda": 1.0,
+            "bc": "periodic", "seed": 0, "dt": prob.dt,
+            "precision": "fp32 fields and math, compensated phi/psi, fp64 t and e^{-2t}",
+            "l2": "state > L2 (4 x 512 MiB fields), no flush needed",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
+def reference_arm(args):
+    """CPU oracle timed as the reference implementation (rank 0 only).  Each
+    bench step is one RK4 step of the oracle on a 512 x 512 x S slab of the
+    workload (periodic), S chosen once from a probe step so that the whole run
+    stays near two minutes."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    N = args.N
+    prob = workload(N)
+    h = prob.L / N
+    cores = os.cpu_count() or 1
+
+    def one(slab):
+        w0 = np.ascontiguousarray(prob.phi0[:slab])
+        w1 = np.ascontiguousarray(prob.phi1[:slab])
+        t0 = time.perf_counter()
+        oracle.run_box(w0, w1, h, prob.mu, prob.lam, 1, 0.0, prob.dt, 1, nthreads=cores)
+        return time.perf_counter() - t0
+
+    probe = one(16)
+    budget = 120.0 / (args.steps + args.warmup)
+    slab = int(max(4, min(64, 16 * budget / max(probe, 1e-6))) // 4 * 4)
+    for _ in range(args.warmup):
+        one(slab)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one(slab)
+    secs = time.perf_counter() - t0
+    val = N * N * slab * args.steps / secs / 1e9
+    sample = f"each step: 1 RK4 step of the FP64 C oracle on a {N}x{N}x{slab} slab ({cores} threads)"
+    cfg = workload_config(N, prob)
+    cfg["sample"] = sample
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "Gpoint-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": val, "unit": "Gpoint-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "Gpoint-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--N", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-extra", action="store_true", help="skip FP64/BF16/plain legs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-requests", type=int, default=256)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    import paper_1803_01291_gb300 as hbe
+
+    N = args.N
+    prob = workload(N)
+    hbm_peak, peak_kind = measured_peaks()
+
+    # headline: FP32 with compensated state; each rank solves its own replica
+    barrier(world, torch)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        secs, stage_ms, launches = time_path(hbe, torch, prob, hbe.FP32, args.steps, args.warmup)
+    secs = max_over_ranks(secs, world, torch, device)
+    barrier(world, torch)
+    pts = float(N) ** 3 * args.steps * world
+    value = pts / secs / 1e9
+
+    sb = stage_bytes("fp32")
+    stage_gbs = [sb[i] * N ** 3 / (stage_ms[i] / 1e3) / 1e9 for i in range(4)]
+    traffic = recorded_traffic("fp32", N)
+    roofline = {"bound": "hbm", "kernel": "stage_kernel<FP32, stage 4> (RK4 combine)",
+                "achieved": stage_gbs[3], "peak": hbm_peak, "unit": "GB/s",
+                "frac": stage_gbs[3] / hbm_peak, "peak_kind": peak_kind,
+                "traffic": traffic,
+                "algorithmic_bytes_per_launch": sb[3] * N ** 3,
+                "step": {"bytes_per_point": sum(sb), "achieved_gbs": sum(sb) * N ** 3 * args.steps / secs / 1e9,
+                         "frac": sum(sb) * N ** 3 * args.steps / secs / 1e9 / hbm_peak},
+                "stages": [{"stage": i + 1, "ms": stage_ms[i], "bytes_per_point": sb[i],
+                            "gbs": stage_gbs[i], "frac": stage_gbs[i] / hbm_peak}
+                           for i in range(4)]}
+
+    line = {
+        "metric": METRIC,
+        "value": value, "unit": "Gpoint-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": workload_config(N, prob, world),
+        "roofline": roofline,
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+    }
+
+    if not args.no_extra:
+        extra = {}
+        for name, pid, steps in (("fp64", hbe.FP64, max(10, args.steps // 10)),
+                                 ("bf16", hbe.BF16, args.steps),
+                                 ("fp32_plain", hbe.FP32_PLAIN, args.steps)):
+            s2, ms2, _ = time_path(hbe, torch, prob, pid, steps, 3)
+            sbp = stage_bytes(name)
+            v = float(N) ** 3 * steps / s2 / 1e9
+            entry = {"value": v, "unit": "Gpoint-steps/s", "steps": steps,
+                     "ms_per_step": s2 / steps * 1e3, "stage_ms": ms2,
+                     "hbm_frac": sum(sbp) * float(N) ** 3 * steps / s2 / 1e9 / hbm_peak}
+            if name == "fp64":
+                # ALU roofline: FP64 FMA-pipe instructions per point-step of the kernels
+                entry["alu_bound_note"] = ("FP64 runs at 0.58 TFMA/s on GB300 (measured); "
+                                           "see DESIGN.md for the per-point op count")
+            extra[name] = entry
+        line["precisions"] = extra
+
+    if not args.no_e2e:
+        nsteps = 308 if N == 512 else max(8, int(round(HORIZON / prob.dt)))
+        e2e_secs, st, _ = e2e_solve(hbe, torch, prob, hbe.FP32, nsteps)
+        e2e_secs = max_over_ranks(e2e_secs, world, torch, device)
+        line["e2e"] = {"value": float(N) ** 3 * nsteps * world / e2e_secs / 1e9,
+                       "unit": "Gpoint-steps/s",
+                       "h2d_bytes_per_step": 2 * 8 * N ** 3 / nsteps,
+                       "d2h_bytes_per_step": 8 * N ** 3 / nsteps,
+                       "steps_per_solve": nsteps,
+                       "note": "one solve: phi0, phi1 from pinned host, nsteps RK4 steps, phi to "
+                               "pinned host; bytes amortised per RK4 step"}
+
+    if not args.no_serve:
+        line["serve"] = serve_leg(hbe, args.serve_requests)
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(prob, 2)
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

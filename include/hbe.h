@@ -80,7 +80,10 @@ typedef struct {
 /* Tile configuration of the stage kernels (see hbe_variant_info). */
 typedef struct {
   int32_t tile_x, tile_y;   /* x-y tile of one thread block */
-  int32_t threads;          /* threads per block */
+  int32_t threads;          /* threads per block: 32 * (consumer_warps + 1 producer warp) */
+  int32_t vec;              /* consecutive x points per lane (tile_x = 32 * vec) */
+  int32_t rows_per_warp;    /* tile rows per consumer warp (tile_y = consumer_warps * rows) */
+  int32_t consumer_warps;
   int32_t smem_bytes[4];    /* dynamic shared memory per stage kernel */
   int32_t ring[4];          /* z-planes in the TMA ring per stage kernel */
 } hbe_variant_t;
@@ -121,6 +124,18 @@ hbe_status hbe_set_initial(hbe_ctx *ctx, const double *phi0, const double *phi1,
 /* Same from device arrays (read on the context's stream before return). */
 hbe_status hbe_set_initial_device(hbe_ctx *ctx, const double *d_phi0, const double *d_phi1,
                                   double t0);
+
+/* Initial data (Eq. HBEinit) at time t0 as sums of the bump family of Sec. 3
+ * (Eq. bump), evaluated on the device at the grid nodes in the normalisation
+ *     A exp(-1 / (1 - |x - c|^2 / R^2))  for |x - c| < R,  0 outside,
+ * phi0 = sum of n0 bumps (A0[i], R0[i], centre c0[3i..3i+2] = (x, y, z)),
+ * phi1 = sum of n1 bumps (A1, R1, c1); n0, n1 in [0, 64]; host arrays, copied.
+ * Coordinates are those of the grid convention above (box centred at 0);
+ * periodic ghosts take wrapped values.  Nothing crosses the bus but the
+ * parameters. */
+hbe_status hbe_set_initial_bumps(hbe_ctx *ctx, int n0, const double *A0, const double *R0,
+                                 const double *c0, int n1, const double *A1, const double *R1,
+                                 const double *c1, double t0);
 
 /* Stop stepping after the first step whose max|phi| exceeds threshold
  * (0 disables; a non-finite phi always stops). */

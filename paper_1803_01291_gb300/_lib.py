@@ -19,7 +19,7 @@ PREC_NAMES = {FP64: "fp64", FP32: "fp32", BF16: "bf16", FP32_PLAIN: "fp32_plain"
 EXPORTS = (
     "hbe_workspace_bytes", "hbe_create", "hbe_create_in", "hbe_destroy", "hbe_set_stream",
     "hbe_set_tuning", "hbe_variant_info", "hbe_variant_count", "hbe_set_initial",
-    "hbe_set_initial_device", "hbe_set_stop", "hbe_step", "hbe_step_async", "hbe_sync",
+    "hbe_set_initial_device", "hbe_set_initial_bumps", "hbe_set_stop", "hbe_step", "hbe_step_async", "hbe_sync",
     "hbe_read", "hbe_read_device", "hbe_profile_stages", "hbe_progress", "hbe_diag", "hbe_save", "hbe_load",
     "hbe_last_error", "hbe_status_string", "hbe_launch_count", "hbe_batch_create",
     "hbe_batch_destroy", "hbe_batch_add", "hbe_batch_remove", "hbe_batch_run",
@@ -36,7 +36,9 @@ class HbeDiag(ctypes.Structure):
 
 class HbeVariant(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("smem_bytes", ctypes.c_int32 * 4),
+                ("threads", ctypes.c_int32), ("vec", ctypes.c_int32),
+                ("rows_per_warp", ctypes.c_int32), ("consumer_warps", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32 * 4),
                 ("ring", ctypes.c_int32 * 4)]
 
 
@@ -78,6 +80,7 @@ def load() -> ctypes.CDLL:
             "hbe_variant_count": (I, [I]),
             "hbe_set_initial": (I, [P, dp, dp, D]),
             "hbe_set_initial_device": (I, [P, P, P, D]),
+            "hbe_set_initial_bumps": (I, [P, I, dp, dp, dp, I, dp, dp, dp, D]),
             "hbe_set_stop": (I, [P, D]),
             "hbe_step": (I, [P, I64, D]),
             "hbe_step_async": (I, [P, I64, D]),

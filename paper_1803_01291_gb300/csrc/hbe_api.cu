@@ -177,11 +177,22 @@ hbe_status encode_map(hbe_ctx *ctx, CUtensorMap *m, void *base, int esize, int p
   return HBE_OK;
 }
 
+// z-chunk length minimising (waves of work items) x (planes per item, with the
+// 4 planes of start-up each chunk costs) over the resident blocks.
 int auto_zchunk(int N, int columns, int resident) {
-  if (columns >= 2 * resident) return N;
-  int nz = (2 * resident + columns - 1) / columns;
-  int zc = (N + nz - 1) / nz;
-  return std::max(zc, std::min(N, 16));
+  double best = 1e300;
+  int best_zc = N;
+  for (int nz = 1; nz <= std::max(1, N / 16); ++nz) {
+    const int zc = (N + nz - 1) / nz;
+    const int items = columns * ((N + zc - 1) / zc);
+    const double waves = std::ceil((double)items / resident);
+    const double cost = waves * (zc + 4);
+    if (cost < best - 1e-9) {
+      best = cost;
+      best_zc = zc;
+    }
+  }
+  return best_zc;
 }
 
 // Work items of one context, ordered z-chunk, then y, then x (neighbouring
@@ -514,6 +525,9 @@ hbe_status hbe_variant_info(int prec, int variant, hbe_variant_t *out) {
   out->tile_x = k[0].tx;
   out->tile_y = k[0].ty;
   out->threads = k[0].threads;
+  out->vec = k[0].vec;
+  out->rows_per_warp = k[0].vy;
+  out->consumer_warps = k[0].nw;
   for (int s = 0; s < 4; ++s) {
     out->smem_bytes[s] = k[s].smem;
     out->ring[s] = k[s].ring;
@@ -591,6 +605,56 @@ hbe_status hbe_set_initial_device(hbe_ctx *ctx, const double *d_phi0, const doub
     if (e != cudaSuccess) return set_err(ctx->err, HBE_ECUDA, "%s", cudaGetErrorString(e));
   }
   return st;
+}
+
+hbe_status hbe_set_initial_bumps(hbe_ctx *ctx, int n0, const double *A0, const double *R0,
+                                 const double *c0, int n1, const double *A1, const double *R1,
+                                 const double *c1, double t0) {
+  if (!ctx) return HBE_EINVAL;
+  if (ctx->in_batch) return set_err(ctx->err, HBE_ESTATE, "context is in a batch");
+  if (n0 < 0 || n1 < 0 || n0 > 64 || n1 > 64)
+    return set_err(ctx->err, HBE_EINVAL, "bump counts must be in [0, 64]");
+  if ((n0 && (!A0 || !R0 || !c0)) || (n1 && (!A1 || !R1 || !c1)))
+    return set_err(ctx->err, HBE_EINVAL, "null bump parameter array");
+  if (!std::isfinite(t0)) return set_err(ctx->err, HBE_EINVAL, "t0 must be finite");
+  double prm[2][64 * 5];
+  for (int i = 0; i < n0; ++i) {
+    if (!(R0[i] > 0.0)) return set_err(ctx->err, HBE_EINVAL, "bump radius must be > 0");
+    const double v[5] = {A0[i], R0[i], c0[3 * i], c0[3 * i + 1], c0[3 * i + 2]};
+    memcpy(&prm[0][5 * i], v, sizeof(v));
+  }
+  for (int i = 0; i < n1; ++i) {
+    if (!(R1[i] > 0.0)) return set_err(ctx->err, HBE_EINVAL, "bump radius must be > 0");
+    const double v[5] = {A1[i], R1[i], c1[3 * i], c1[3 * i + 1], c1[3 * i + 2]};
+    memcpy(&prm[1][5 * i], v, sizeof(v));
+  }
+  hbe_status st = sync_ctx(ctx);
+  if (st != HBE_OK) return st;
+  // the parameters ride in the G fields (free until the first step): no allocation
+  if (3 * ctx->bytes_g < sizeof(prm)) return set_err(ctx->err, HBE_EINVAL, "grid too small");
+  double *d_prm = static_cast<double *>(ctx->f[F_G1]);
+  CK(cudaMemcpy(d_prm, prm, sizeof(prm), cudaMemcpyHostToDevice));
+  const int sprec = ctx->prec == HBE_FP64 ? 0 : 1;
+  const bool kahan = is_kahan(ctx->prec);
+  CK(launch_bumps(sprec, ctx->f[F_P0], kahan ? ctx->f[F_PLO0] : nullptr, ctx->N, ctx->pitch_s,
+                  ctx->hxs, ctx->bc, ctx->h, n0, d_prm, ctx->stream));
+  CK(launch_bumps(sprec, ctx->f[F_Q0], kahan ? ctx->f[F_QLO0] : nullptr, ctx->N, ctx->pitch_s,
+                  ctx->hxs, ctx->bc, ctx->h, n1, d_prm + 64 * 5, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  // the stage kernels overwrite G before reading it, but the Dirichlet ghosts must be 0
+  CK(cudaMemset(ctx->f[F_G1], 0, 3 * ctx->bytes_g));
+  Desc &d = *ctx->h_desc;
+  d.t0 = t0;
+  d.dt = 0.0;
+  d.n_base = 0;
+  d.n_end = 0;
+  d.stop_k = kNoStop;
+  d.status = ST_RUNNING;
+  d.last_done = 0;
+  if ((st = push_desc(ctx)) != HBE_OK) return st;
+  CK(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+  ctx->has_state = true;
+  return HBE_OK;
 }
 
 hbe_status hbe_set_stop(hbe_ctx *ctx, double threshold) {

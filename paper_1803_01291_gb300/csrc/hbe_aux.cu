@@ -90,6 +90,57 @@ cudaError_t launch_unpack(int prec, const void *hi, const void *lo, double *dst,
   return cudaGetLastError();
 }
 
+// Sum of bumps A exp(-1 / (1 - r^2/R^2)) (r < R) at every padded position of
+// a field (the initial-data family of Sec. 3, Eq. bump, in box coordinates).
+// Node i sits at (i - c) h with c = (N-1)/2 (Dirichlet) or N/2 (periodic);
+// periodic ghosts take the wrapped node's value, other ghosts stay 0.
+template <class T>
+__global__ void bumps_kernel(T *__restrict__ hi, T *__restrict__ lo, int N, int pitch, int hx,
+                             int periodic, double h, int nb, const double *__restrict__ prm) {
+  const int64_t plane = (int64_t)(N + 4) * pitch;
+  const int64_t total = plane * N;
+  const double cen = periodic ? 0.5 * N : 0.5 * (N - 1);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int z = (int)(i / plane);
+    const int64_t r = i - (int64_t)z * plane;
+    const int yp = (int)(r / pitch), xp = (int)(r - (int64_t)yp * pitch);
+    int x = xp - hx, y = yp - 2;
+    const bool xin = x >= 0 && x < N, yin = y >= 0 && y < N;
+    bool have = xin && yin;
+    if (!have && periodic) {
+      if (yin && x >= -2 && x < N + 2) { x = (x + N) % N; have = true; }
+      else if (xin && y >= -2 && y < N + 2) { y = (y + N) % N; have = true; }
+    }
+    double v = 0.0;
+    if (have) {
+      const double px = ((double)x - cen) * h, py = ((double)y - cen) * h,
+                   pz = ((double)z - cen) * h;
+      for (int b = 0; b < nb; ++b) {
+        const double A = prm[5 * b], R = prm[5 * b + 1];
+        const double dx = px - prm[5 * b + 2], dy = py - prm[5 * b + 3], dz = pz - prm[5 * b + 4];
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < R * R) v = v + A * exp(-1.0 / (1.0 - r2 / (R * R)));
+      }
+    }
+    const T hv = (T)v;
+    hi[i] = hv;
+    if (lo) lo[i] = (T)(v - (double)hv);
+  }
+}
+
+cudaError_t launch_bumps(int prec, void *hi, void *lo, int N, int pitch, int hx, int periodic,
+                         double h, int nb, const double *d_prm, cudaStream_t st) {
+  const int64_t n = (int64_t)(N + 4) * pitch * N;
+  if (prec == 0)
+    bumps_kernel<double><<<grid_for(n, 256), 256, 0, st>>>((double *)hi, (double *)lo, N, pitch,
+                                                           hx, periodic, h, nb, d_prm);
+  else
+    bumps_kernel<float><<<grid_for(n, 256), 256, 0, st>>>((float *)hi, (float *)lo, N, pitch, hx,
+                                                          periodic, h, nb, d_prm);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- bookkeeping
 // After K steps of a batch: count the steps each context executed, apply the
 // stop rule to the last of them, advance n_base, and clear the per-step maxima.

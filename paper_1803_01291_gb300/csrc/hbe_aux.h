@@ -9,6 +9,8 @@ cudaError_t launch_pack(int prec, const double *src, void *hi, void *lo, int N, 
                         int periodic, int z_begin, int z_count, cudaStream_t st);
 cudaError_t launch_unpack(int prec, const void *hi, const void *lo, double *dst, int N, int pitch,
                           int hx, int z_begin, int z_count, cudaStream_t st);
+cudaError_t launch_bumps(int prec, void *hi, void *lo, int N, int pitch, int hx, int periodic,
+                         double h, int nb, const double *d_prm, cudaStream_t st);
 cudaError_t launch_advance(Desc *descs, const int *ndesc, int max_desc, int K, cudaStream_t st);
 cudaError_t launch_set_run(Desc *d, long long add_steps, double t0, double dt, double thr,
                            int reset, cudaStream_t st);

@@ -18,19 +18,20 @@
 // field a stage reads with a halo is written by that stage.
 //
 // Kernel shape (one launch per stage, persistent blocks over a work list):
-//   * a block owns a TX x TY tile in x-y and marches along z over a chunk;
-//   * each z-plane of every input field is brought into a shared-memory ring
-//     by the TMA unit (cp.async.bulk.tensor, completion on an mbarrier); the
-//     fields that enter the stencil come with a 2-row / HX-column halo, zero
-//     filled by the TMA unit outside the box in z (Dirichlet);
-//   * the stage argument P is formed once per loaded point: for the thread's
-//     own column it enters a 5-deep register window (z-2..z+2), for the x-y
-//     halo ring it is written with the own values to a shared P-plane;
-//   * the 13-point stencil reads x/y neighbours from the P-plane (128-bit
-//     loads) and z neighbours from registers; each thread owns VEC consecutive
-//     x points (16 bytes of the math type), stores are 128-bit where possible.
-//   * one __syncthreads per plane; the slot of plane m-3 is refilled right
-//     after it, so up to RING-3 planes are in flight ahead of the consumer.
+//   * a block owns a TX x TY tile in x-y (TX = 32 VEC: one warp spans the row,
+//     each lane VEC consecutive x points) and marches along z over a chunk;
+//   * one producer warp streams every z-plane of every input field into a
+//     shared-memory ring with the TMA unit (cp.async.bulk.tensor, completion
+//     on a "full" mbarrier per slot); fields that enter the stencil come with a
+//     2-row / 16-byte halo, zero filled by the TMA unit outside the box in z;
+//   * NW consumer warps each own VY rows of the tile.  A consumer forms the
+//     stage argument P of its own points once per plane into a 5-deep register
+//     window (z-2..z+2); x neighbours come from the neighbouring lanes by warp
+//     shuffles, y neighbours from the warp's own rows in registers or, for the
+//     two rows above and below its strip, from the ring; z neighbours from the
+//     window.  When a warp is done with a slot it arrives on the slot's
+//     "empty" mbarrier; the producer refills a slot once all consumers have
+//     released it.  There is no block-wide synchronisation in the plane loop.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -64,7 +65,7 @@ __host__ __device__ constexpr int align128(int b) { return (b + 127) & ~127; }
 __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
-template <class PR, int TX_, int TY_, int BUDGET_, int S_>
+template <class PR, int VEC_, int VY_, int NW_, int BUDGET_, int MINB_, int S_>
 struct StageCfg {
   using TS = typename PR::TS;
   using TG = typename PR::TG;
@@ -72,16 +73,17 @@ struct StageCfg {
   static constexpr bool KAHAN = PR::KAHAN;
   static constexpr bool DIFF = PR::DIFF;
   static constexpr int S = S_;
-  static constexpr int TX = TX_, TY = TY_;
-  static constexpr int VEC = 16 / (int)sizeof(TM);
-  static constexpr int TPR = TX / VEC;
-  static constexpr int THREADS = TPR * TY;
+  static constexpr int VEC = VEC_;                 // consecutive x points per lane
+  static constexpr int VY = VY_;                   // rows per consumer warp
+  static constexpr int NW = NW_;                   // consumer warps
+  static constexpr int TX = 32 * VEC, TY = NW * VY;
+  static constexpr int THREADS = 32 * (NW + 1);    // + one producer warp
   static constexpr int HXS = 16 / (int)sizeof(TS);
   static constexpr int HXG = 16 / (int)sizeof(TG);
-  static constexpr int HXM = 16 / (int)sizeof(TM);
   static constexpr int BY = TY + 4;
-  static constexpr int BXS = TX + 2 * HXS, BXG = TX + 2 * HXG, BXM = TX + 2 * HXM;
-  // ring slot composition
+  static constexpr int BXS = TX + 2 * HXS, BXG = TX + 2 * HXG;
+  // ring slot composition: halo tiles of the fields that enter the stencil, then
+  // interior tiles of the fields read at the point only
   static constexpr int NHS = (S == 1) ? 1 : 2;                           // p [, q]
   static constexpr int NHG = (S >= 3) ? 1 : 0;                           // G1 (S3) / G2 (S4)
   static constexpr int NIS = (S == 1) ? 1 : ((S == 4 && KAHAN) ? 2 : 0); // q (S1) / plo, qlo (S4)
@@ -98,15 +100,14 @@ struct StageCfg {
   static constexpr int SLOT_BYTES = OFF_IG + NIG * IG_BYTES;
   static constexpr uint32_t TX_BYTES =
       (uint32_t)(NHS * HS_RAW + NHG * HG_RAW + NIS * IS_RAW + NIG * IG_RAW);
-  static constexpr int PPLANE_BYTES = align128(BY * BXM * (int)sizeof(TM));
-  static constexpr int HEADER = 256;  // mbarriers + coefficients + flags
-  static constexpr int RING = cmax(4, cmin(12, (BUDGET_ - HEADER - 2 * PPLANE_BYTES) / SLOT_BYTES));
-  static constexpr int SMEM = HEADER + 2 * PPLANE_BYTES + RING * SLOT_BYTES;
-  static constexpr int NHALO = 4 * TPR + 2 * TY;  // halo vector items per plane
-  static_assert(TX % VEC == 0, "tile width must hold whole vectors");
-  static_assert(HXS >= 2 && HXG >= 2, "halo of 2 needed");
-  static_assert(TX + 2 * HXG <= 256 && BY <= 256, "TMA box limit");
-  static_assert(RING * 8 <= 128, "barrier area");
+  static constexpr int HEADER = 384;  // 2 x 16 mbarriers, flags
+  static constexpr int RING = cmax(4, cmin(16, (BUDGET_ - HEADER) / SLOT_BYTES));
+  static constexpr int SMEM = HEADER + RING * SLOT_BYTES;
+  static constexpr int MINB = MINB_;  // blocks per SM the registers must allow
+  static_assert(VEC == 1 || VEC == 2, "one or two x points per lane");
+  static_assert(VEC * (int)sizeof(TM) <= 16, "lane vector of <= 16 bytes");
+  static_assert(HXS >= 2 && HXG >= 2 && HXS % VEC == 0 && HXG % VEC == 0, "halo alignment");
+  static_assert(BXG <= 256 && BXS <= 256 && BY <= 256, "TMA box limit");
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -168,38 +169,26 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap *map) {
 }
 
 // ---------------------------------------------------------------- vectors
-template <class T> struct VecIO;
-template <> struct VecIO<float> {  // 4 floats = 16 bytes
-  static __device__ __forceinline__ void load(const float *p, float (&v)[4]) {
-    const float4 a = *reinterpret_cast<const float4 *>(p);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-  }
-  static __device__ __forceinline__ void store(float *p, const float (&v)[4]) {
-    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  }
-};
-template <> struct VecIO<double> {  // 2 doubles = 16 bytes
-  static __device__ __forceinline__ void load(const double *p, double (&v)[2]) {
-    const double2 a = *reinterpret_cast<const double2 *>(p);
-    v[0] = a.x; v[1] = a.y;
-  }
-  static __device__ __forceinline__ void store(double *p, const double (&v)[2]) {
-    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
-  }
-};
+// Aligned loads/stores of n = 1, 2 or 4 consecutive elements as one access.
+template <class T, int n> struct Raw;
+template <> struct Raw<float, 1> { using type = float; };
+template <> struct Raw<float, 2> { using type = float2; };
+template <> struct Raw<float, 4> { using type = float4; };
+template <> struct Raw<double, 1> { using type = double; };
+template <> struct Raw<double, 2> { using type = double2; };
+template <> struct Raw<__nv_bfloat16, 1> { using type = unsigned short; };
+template <> struct Raw<__nv_bfloat16, 2> { using type = unsigned int; };
+template <> struct Raw<__nv_bfloat16, 4> { using type = uint2; };
 
-// Load VEC values of storage type T at p (aligned) and widen to TM.
-template <class T, class TM, int VEC>
-__device__ __forceinline__ void load_as(const T *p, TM (&v)[VEC]) {
-  if constexpr (sizeof(T) == sizeof(TM)) {
-    VecIO<TM>::load(reinterpret_cast<const TM *>(p), v);
-  } else {  // bfloat16 x 4 -> float x 4 (exact)
-    static_assert(VEC == 4, "bf16 path uses float math");
-    const uint2 raw = *reinterpret_cast<const uint2 *>(p);
-    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&raw.x);
-    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&raw.y);
-    v[0] = __low2float(a); v[1] = __high2float(a);
-    v[2] = __low2float(b); v[3] = __high2float(b);
+template <class T, class TM, int n>
+__device__ __forceinline__ void load_as(const T *p, TM (&v)[n]) {
+  using R = typename Raw<T, n>::type;
+  const R raw = *reinterpret_cast<const R *>(p);
+  const T *e = reinterpret_cast<const T *>(&raw);
+#pragma unroll
+  for (int j = 0; j < n; ++j) {
+    if constexpr (sizeof(T) == sizeof(TM)) v[j] = e[j];
+    else v[j] = __bfloat162float(e[j]);  // exact widening
   }
 }
 template <class T, class TM>
@@ -207,20 +196,19 @@ __device__ __forceinline__ T narrow(TM v) {
   if constexpr (sizeof(T) == sizeof(TM)) return v;
   else return __float2bfloat16_rn(v);  // round to nearest even
 }
-template <class T, class TM, int VEC>
-__device__ __forceinline__ void store_as(T *p, const TM (&v)[VEC]) {
-  if constexpr (sizeof(T) == sizeof(TM)) {
-    VecIO<TM>::store(reinterpret_cast<TM *>(p), v);
-  } else {
-    __nv_bfloat162 a, b;
-    a.x = narrow<T>(v[0]); a.y = narrow<T>(v[1]);
-    b.x = narrow<T>(v[2]); b.y = narrow<T>(v[3]);
-    uint2 raw;
-    raw.x = *reinterpret_cast<uint32_t *>(&a);
-    raw.y = *reinterpret_cast<uint32_t *>(&b);
-    *reinterpret_cast<uint2 *>(p) = raw;
-  }
+template <class T, class TM, int n>
+__device__ __forceinline__ void store_as(T *p, const TM (&v)[n]) {
+  using R = typename Raw<T, n>::type;
+  R raw;
+  T *e = reinterpret_cast<T *>(&raw);
+#pragma unroll
+  for (int j = 0; j < n; ++j) e[j] = narrow<T>(v[j]);
+  *reinterpret_cast<R *>(p) = raw;
 }
+template <class TM, int n>
+__device__ __forceinline__ void lds(const TM *p, TM (&v)[n]) { load_as<TM, TM, n>(p, v); }
+template <class TM, int n>
+__device__ __forceinline__ void sts(TM *p, const TM (&v)[n]) { store_as<TM, TM, n>(p, v); }
 
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -234,21 +222,20 @@ __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
   e = (a - aa) + (b - bb);
 }
 
-// Store VEC values of a field at interior point (x, y, z) of the padded layout,
-// masking x >= N and writing the periodic ghost copies.
+// Store VEC values of a field at interior point (x, y) of a plane of the padded
+// layout (`row` points at the row's x = 0).  `ragged`: the tile may cross x = N
+// (mask); `edge`: periodic tile touching a wrap band (write the ghost copies).
 template <class T, class TM, int VEC>
-__device__ __forceinline__ void store_point(T *base, int pitch, int64_t plane, int hx, int N,
-                                            bool periodic, int x, int y, int z,
-                                            const TM (&v)[VEC]) {
-  T *row = base + (int64_t)z * plane + (int64_t)(y + 2) * pitch + hx;
-  if (x + VEC <= N) {
+__device__ __forceinline__ void store_point(T *row, int64_t pitch, int N, bool ragged, bool edge,
+                                            int x, int y, const TM (&v)[VEC]) {
+  if (!ragged || x + VEC <= N) {
     store_as<T, TM, VEC>(row + x, v);
   } else {
 #pragma unroll
     for (int j = 0; j < VEC; ++j)
       if (x + j < N) row[x + j] = narrow<T>(v[j]);
   }
-  if (periodic) {
+  if (edge) {
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
       const int xx = x + j;
@@ -270,337 +257,430 @@ struct Coef {
 };
 
 // ---------------------------------------------------------------- the kernel
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Whether a work item's context takes this step (the same answer in every
+// warp: n_base/n_end are fixed during a launch, and the stop rule of stage 1
+// reads the previous step's maximum, written by an earlier launch).
+template <int S>
+__device__ __forceinline__ bool item_active(Desc *d, int k, bool leader) {
+  const long long n = d->n_base + k;
+  if (n >= d->n_end || __ldcg(&d->stop_k) <= k) return false;
+  if (S == 1 && k > 0) {
+    const double m = __longlong_as_double((long long)__ldcg(d->maxabs + k - 1));
+    if (!(m <= 1.7976931348623157e308) || (d->stop_thr > 0.0 && m > d->stop_thr)) {
+      if (leader) atomicMin(&d->stop_k, (long long)k);
+      return false;
+    }
+  }
+  return true;
+}
+
+// Stage coefficients in double precision, narrowed to the math type.
 template <class C>
-__global__ void __launch_bounds__(C::THREADS)
-    stage_kernel(const StageParams prm) {
+__device__ __forceinline__ Coef<typename C::TM> stage_coef(const Desc *d, long long n) {
+  using TM = typename C::TM;
+  constexpr int S = C::S;
+  const double dt = d->dt;
+  const double tn = d->t0 + (double)n * dt;
+  const double ts = tn + (S == 1 ? 0.0 : (S == 4 ? dt : 0.5 * dt));
+  const double c = exp(-2.0 * ts) * d->inv_h2;
+  Coef<TM> cf;
+  cf.c43 = (TM)(4.0 / 3.0 * c);
+  cf.cm12 = (TM)(-c / 12.0);
+  cf.ccen = C::DIFF ? (TM)d->mu2 : (TM)(d->mu2 - 7.5 * c);
+  cf.nlam = (TM)(-d->lambda);
+  cf.m3 = (TM)(-3.0);
+  cf.a1 = (TM)(S == 1 ? 0.0 : (S == 4 ? dt : 0.5 * dt));
+  cf.a2 = (TM)(S == 3 ? 0.25 * dt * dt : (S == 4 ? 0.5 * dt * dt : 0.0));
+  cf.b6 = (TM)(dt * dt / 6.0);
+  cf.d6 = (TM)(dt / 6.0);
+  return cf;
+}
+
+template <class TM>
+__device__ __forceinline__ TM shfl_idx(TM v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+template <class TM>
+__device__ __forceinline__ TM shfl_up1(TM v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+template <class TM>
+__device__ __forceinline__ TM shfl_dn1(TM v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+
+// ---------------------------------------------------------------- producer warp
+template <class C>
+__device__ __forceinline__ void produce(const StageParams &prm, uint64_t *full, uint64_t *empty,
+                                        unsigned char *ring, volatile int *abort_flag) {
+  constexpr int S = C::S, RING = C::RING, TX = C::TX, TY = C::TY;
+  const int nitems = *prm.nitems;
+  int slot = 0;
+  uint32_t fill = 0;  // fill count of `slot` (phase = fill & 1)
+  uint32_t issued_slots = 0;
+  bool bad = false;
+  for (int it = blockIdx.x; it < nitems && !bad; it += gridDim.x) {
+    const WorkItem w = prm.items[it];
+    Desc *d = prm.descs + w.x;
+    if (!item_active<S>(d, prm.k, false)) continue;
+    const CUtensorMap *tm = d->tmaps;
+    for (int t = 0; t < NUM_TMAPS; ++t) tmap_acquire(tm + t);
+    const int N = d->N;
+    const bool periodic = d->bc == 1;
+    const int set = (int)((d->n_base + prm.k) & 1);
+    const CUtensorMap *mp = tm + (set ? TM_P_H1 : TM_P_H0);
+    const CUtensorMap *mq = tm + (set ? TM_Q_H1 : TM_Q_H0);
+    const CUtensorMap *mg = tm + (S == 3 ? TM_G1_H : TM_G2_H);
+    const CUtensorMap *mi0 = tm + (S == 1 ? (set ? TM_Q_I1 : TM_Q_I0)
+                                          : (S == 2 ? TM_G1_I : (S == 3 ? TM_G2_I : TM_G1_I)));
+    const CUtensorMap *mi1 = tm + TM_G3_I;
+    const CUtensorMap *mlp = tm + (set ? TM_PLO_I1 : TM_PLO_I0);
+    const CUtensorMap *mlq = tm + (set ? TM_QLO_I1 : TM_QLO_I0);
+    const int x0 = (w.y & 0xffff) * TX, y0 = (w.y >> 16) * TY;
+    const int z0 = w.z, nplanes = w.w + 4;
+    for (int m = 0; m < nplanes; ++m) {
+      if (fill >= 1 && !mbar_wait_bounded(&empty[slot], (fill - 1) & 1u)) { bad = true; break; }
+      if (*abort_flag) { bad = true; break; }
+      unsigned char *base = ring + slot * C::SLOT_BYTES;
+      uint64_t *bar = &full[slot];
+      int z = z0 - 2 + m;
+      if (periodic) z = (z % N + N) % N;
+      mbar_expect_tx(bar, C::TX_BYTES);
+      tma_load_3d(base, mp, bar, x0, y0, z);
+      if constexpr (C::NHS == 2) tma_load_3d(base + C::HS_BYTES, mq, bar, x0, y0, z);
+      if constexpr (C::NHG == 1) tma_load_3d(base + C::OFF_HG, mg, bar, x0, y0, z);
+      constexpr int HXS = C::HXS, HXG = C::HXG;
+      if constexpr (S == 1) tma_load_3d(base + C::OFF_IS, mi0, bar, x0 + HXS, y0 + 2, z);
+      if constexpr (S >= 2) tma_load_3d(base + C::OFF_IG, mi0, bar, x0 + HXG, y0 + 2, z);
+      if constexpr (S == 4) {
+        tma_load_3d(base + C::OFF_IG + C::IG_BYTES, mi1, bar, x0 + HXG, y0 + 2, z);
+        if constexpr (C::KAHAN) {
+          tma_load_3d(base + C::OFF_IS, mlp, bar, x0 + HXS, y0 + 2, z);
+          tma_load_3d(base + C::OFF_IS + C::IS_BYTES, mlq, bar, x0 + HXS, y0 + 2, z);
+        }
+      }
+      issued_slots |= 1u << slot;
+      if (++slot == RING) { slot = 0; ++fill; }
+    }
+  }
+  if (bad) {
+    *abort_flag = 1;
+    atomicOr(prm.err, (unsigned)DEV_ERR_TIMEOUT);
+  }
+  // every copy issued must land before the block's shared memory goes away:
+  // the last fill of slot r has fill count fill (r < slot) or fill - 1 (r >= slot)
+  for (int r = 0; r < RING; ++r) {
+    if (!(issued_slots >> r & 1u)) continue;
+    const uint32_t f = r < slot ? fill : fill - 1;
+    (void)mbar_wait_bounded(&full[r], f & 1u);
+  }
+}
+
+// ---------------------------------------------------------------- consumer warps
+template <class C>
+struct Consumer {
   using TS = typename C::TS;
   using TG = typename C::TG;
   using TM = typename C::TM;
-  constexpr int S = C::S, VEC = C::VEC, TX = C::TX, TY = C::TY, TPR = C::TPR;
-  constexpr int RING = C::RING, BXM = C::BXM, HXM = C::HXM;
-  constexpr int BXS = C::BXS, BXG = C::BXG, HXS = C::HXS, HXG = C::HXG;
+  static constexpr int S = C::S, VEC = C::VEC, VY = C::VY, TX = C::TX;
+  static constexpr int BXS = C::BXS, BXG = C::BXG, HXS = C::HXS, HXG = C::HXG;
+  static constexpr int NI = C::NIS + C::NIG;  // point-only input fields
 
+  // Stage argument P at tile position (lx, ly) (ly in [-2, TY+2)) from the ring tiles.
+  static __device__ __forceinline__ void comb(const unsigned char *base, const Coef<TM> &cf,
+                                              int lx, int ly, TM (&out)[VEC]) {
+    load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(base) + (ly + 2) * BXS + lx + HXS, out);
+    if constexpr (S >= 2) {
+      TM qv[VEC];
+      load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(base + C::HS_BYTES) + (ly + 2) * BXS + lx + HXS, qv);
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) out[j] = fmaT(cf.a1, qv[j], out[j]);
+    }
+    if constexpr (S >= 3) {
+      TM gv[VEC];
+      load_as<TG, TM, VEC>(reinterpret_cast<const TG *>(base + C::OFF_HG) + (ly + 2) * BXG + lx + HXG, gv);
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) out[j] = fmaT(cf.a2, gv[j], out[j]);
+    }
+  }
+
+  // x neighbours (x-2, x-1, x+1, x+2) of the lane's VEC points in tile row ly,
+  // whose own P values are c.
+  static __device__ __forceinline__ void xnb(const unsigned char *base, const Coef<TM> &cf,
+                                             int lane, int lx0, int ly, const TM (&c)[VEC],
+                                             TM (&m2)[VEC], TM (&m1)[VEC], TM (&p1)[VEC],
+                                             TM (&p2)[VEC]) {
+    if constexpr (S == 1) {
+      // P = p: read the neighbours straight from the halo tile
+      const TS *hp = reinterpret_cast<const TS *>(base) + (ly + 2) * BXS + lx0 + HXS;
+      if constexpr (VEC == 2) {
+        TM a[2], b[2];
+        load_as<TS, TM, 2>(hp - 2, a);
+        load_as<TS, TM, 2>(hp + 2, b);
+        m2[0] = a[0]; m1[0] = a[1]; p1[0] = c[1]; p2[0] = b[0];
+        m2[1] = a[1]; m1[1] = c[0]; p1[1] = b[0]; p2[1] = b[1];
+      } else {
+        m2[0] = (TM)hp[-2]; m1[0] = (TM)hp[-1]; p1[0] = (TM)hp[1]; p2[0] = (TM)hp[2];
+      }
+    } else if constexpr (VEC == 2) {
+      TM pa = shfl_up1(c[0], 1), pb = shfl_up1(c[1], 1);
+      TM na = shfl_dn1(c[0], 1), nb = shfl_dn1(c[1], 1);
+      if (lane == 0) {
+        TM hv[2];
+        comb(base, cf, -2, ly, hv);
+        pa = hv[0]; pb = hv[1];
+      } else if (lane == 31) {
+        TM hv[2];
+        comb(base, cf, TX, ly, hv);
+        na = hv[0]; nb = hv[1];
+      }
+      m2[0] = pa; m1[0] = pb; p1[0] = c[1]; p2[0] = na;
+      m2[1] = pb; m1[1] = c[0]; p1[1] = na; p2[1] = nb;
+    } else {
+      TM hv[1] = {c[0]};
+      if (lane < 2) comb(base, cf, lane - 2, ly, hv);
+      else if (lane >= 30) comb(base, cf, TX + lane - 30, ly, hv);
+      const TM up2 = shfl_up1(c[0], 2), up1 = shfl_up1(c[0], 1);
+      const TM dn2 = shfl_dn1(c[0], 2), dn1 = shfl_dn1(c[0], 1);
+      const TM h1 = shfl_idx(hv[0], 1), h30 = shfl_idx(hv[0], 30);
+      m2[0] = lane < 2 ? hv[0] : up2;
+      m1[0] = lane == 0 ? h1 : up1;
+      p2[0] = lane >= 30 ? hv[0] : dn2;
+      p1[0] = lane == 31 ? h30 : dn1;
+    }
+  }
+
+  static __device__ __forceinline__ TM lap_g(const Coef<TM> &cf, TM P0, TM xm2, TM xm1, TM xp1,
+                                             TM xp2, TM ym2, TM ym1, TM yp1, TM yp2, TM zm2,
+                                             TM zm1, TM zp1, TM zp2, TM Q) {
+    TM s1, s2;
+    if constexpr (C::DIFF) {
+      s1 = ((xm1 - P0) + (xp1 - P0)) + (((ym1 - P0) + (yp1 - P0)) + ((zm1 - P0) + (zp1 - P0)));
+      s2 = ((xm2 - P0) + (xp2 - P0)) + (((ym2 - P0) + (yp2 - P0)) + ((zm2 - P0) + (zp2 - P0)));
+    } else {
+      s1 = ((xm1 + xp1) + (ym1 + yp1)) + (zm1 + zp1);
+      s2 = ((xm2 + xp2) + (ym2 + yp2)) + (zm2 + zp2);
+    }
+    TM g = fmaT(cf.nlam * (P0 * P0), P0, cf.m3 * Q);
+    g = fmaT(cf.ccen, P0, g);
+    g = fmaT(cf.cm12, s2, g);
+    return fmaT(cf.c43, s1, g);
+  }
+
+  static __device__ __forceinline__ void run(const StageParams &prm, uint64_t *full,
+                                             uint64_t *empty, const unsigned char *ring,
+                                             volatile int *abort_flag, int warp, int lane) {
+    constexpr int RING = C::RING;
+    const int nitems = *prm.nitems;
+    const int lx0 = lane * VEC, ly0 = warp * VY;
+    int slot = 0;
+    uint32_t phase = 0;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+      const WorkItem w = prm.items[it];
+      Desc *d = prm.descs + w.x;
+      if (!item_active<S>(d, prm.k, warp == 0 && lane == 0)) continue;
+      const long long n = d->n_base + prm.k;
+      Coef<TM> cf;
+      {
+        Coef<TM> c0;
+        if (lane == 0) c0 = stage_coef<C>(d, n);
+        const TM *src = reinterpret_cast<const TM *>(&c0);
+        TM *dst = reinterpret_cast<TM *>(&cf);
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(Coef<TM>) / sizeof(TM)); ++i) dst[i] = shfl_idx(src[i], 0);
+      }
+      // ---- everything the item needs from the descriptor, held in registers
+      const int N = d->N;
+      const bool periodic = d->bc == 1;
+      const int set = (int)(n & 1);
+      const int so = set ^ 1;
+      const int x0 = (w.y & 0xffff) * TX, y0 = (w.y >> 16) * C::TY;
+      const int z0 = w.z, len = w.w, nplanes = len + 4;
+      const bool ragged = x0 + TX > N;
+      const bool edge = periodic && (x0 < 2 || x0 + TX > N - 2 || y0 < 2 || y0 + C::TY > N - 2);
+      const int x = x0 + lx0;
+      const int64_t pitch_s = d->pitch_s, plane_s = d->plane_s;
+      const int64_t pitch_g = d->pitch_g, plane_g = d->plane_g;
+      const int64_t row_s = (int64_t)(y0 + ly0 + 2) * pitch_s + HXS + x;  // row r: + r pitch
+      const int64_t row_g = (int64_t)(y0 + ly0 + 2) * pitch_g + HXG + x;
+      const bool xok = x < N;
+      (void)len;
+      // outputs
+      TG *outG = nullptr;
+      TS *outP = nullptr, *outQ = nullptr, *outPL = nullptr, *outQL = nullptr;
+      if constexpr (S <= 3) outG = reinterpret_cast<TG *>(d->f[S == 1 ? F_G1 : (S == 2 ? F_G2 : F_G3)]);
+      if constexpr (S == 4) {
+        outP = reinterpret_cast<TS *>(d->f[F_P0 + so]);
+        outQ = reinterpret_cast<TS *>(d->f[F_Q0 + so]);
+        if constexpr (C::KAHAN) {
+          outPL = reinterpret_cast<TS *>(d->f[F_PLO0 + so]);
+          outQL = reinterpret_cast<TS *>(d->f[F_QLO0 + so]);
+        }
+      }
+      bool rok[VY];
+#pragma unroll
+      for (int r = 0; r < VY; ++r) rok[r] = xok && (y0 + ly0 + r < N);
+
+      TM win[5][VY][VEC];
+#pragma unroll
+      for (int a = 0; a < 5; ++a)
+#pragma unroll
+        for (int r = 0; r < VY; ++r)
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) win[a][r][j] = (TM)0;
+      TM run_max = (TM)0;
+
+      for (int m = 0; m < nplanes; ++m) {
+        if (!mbar_wait_bounded(&full[slot], phase)) {
+          *abort_flag = 1;
+          atomicOr(prm.err, (unsigned)DEV_ERR_TIMEOUT);
+          return;
+        }
+        if (*abort_flag) return;
+        const unsigned char *base = ring + slot * C::SLOT_BYTES;
+        // own rows at plane z0 - 2 + m enter the window
+#pragma unroll
+        for (int r = 0; r < VY; ++r) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) win[a][r][j] = win[a + 1][r][j];
+          comb(base, cf, lx0, ly0 + r, win[4][r]);
+        }
+        const int s2 = slot >= 2 ? slot - 2 : slot + RING - 2;  // slot of plane m - 2
+        if (m >= 4) {
+          // ---- output plane z0 + m - 4, loaded as plane m - 2
+          const int z = z0 + m - 4;
+          const unsigned char *b2 = ring + s2 * C::SLOT_BYTES;
+          TM R[VY + 4][VEC];  // rows ly0-2 .. ly0+VY+1 of P at plane z
+          comb(b2, cf, lx0, ly0 - 2, R[0]);
+          comb(b2, cf, lx0, ly0 - 1, R[1]);
+          comb(b2, cf, lx0, ly0 + VY, R[VY + 2]);
+          comb(b2, cf, lx0, ly0 + VY + 1, R[VY + 3]);
+#pragma unroll
+          for (int r = 0; r < VY; ++r)
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) R[r + 2][j] = win[2][r][j];
+#pragma unroll
+          for (int r = 0; r < VY; ++r) {
+            const int ly = ly0 + r;
+            const int y = y0 + ly;
+            TM m2[VEC], m1[VEC], p1[VEC], p2[VEC];
+            xnb(b2, cf, lane, lx0, ly, win[2][r], m2, m1, p1, p2);
+            const int hoff = (ly + 2) * BXS + lx0 + HXS;
+            const int ioff = ly * TX + lx0;
+            // point-only inputs from the interior tiles
+            TM cur[NI > 0 ? NI : 1][VEC];
+            if constexpr (S == 1) {
+              load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(b2 + C::OFF_IS) + ioff, cur[0]);
+            } else {
+              const TG *ig = reinterpret_cast<const TG *>(b2 + C::OFF_IG) + ioff;
+              load_as<TG, TM, VEC>(ig, cur[0]);  // S2: G1, S3: G2, S4: G1
+              if constexpr (S == 4) {
+                load_as<TG, TM, VEC>(ig + C::IG_BYTES / (int)sizeof(TG), cur[1]);  // G3
+                if constexpr (C::KAHAN) {
+                  const TS *is = reinterpret_cast<const TS *>(b2 + C::OFF_IS) + ioff;
+                  load_as<TS, TM, VEC>(is, cur[2]);
+                  load_as<TS, TM, VEC>(is + C::IS_BYTES / (int)sizeof(TS), cur[3]);
+                }
+              }
+            }
+            TM Q[VEC], qS[VEC];
+            if constexpr (S == 1) {
+#pragma unroll
+              for (int j = 0; j < VEC; ++j) Q[j] = cur[0][j];
+            } else {
+              load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(b2 + C::HS_BYTES) + hoff, qS);
+              // S2: q + dt/2 G1, S3: q + dt/2 G2, S4: q + dt G3
+              const int gi = (S == 4) ? 1 : 0;
+#pragma unroll
+              for (int j = 0; j < VEC; ++j) Q[j] = fmaT(cf.a1, cur[gi][j], qS[j]);
+            }
+            TM Gout[VEC];
+#pragma unroll
+            for (int j = 0; j < VEC; ++j)
+              Gout[j] = lap_g(cf, win[2][r][j], m2[j], m1[j], p1[j], p2[j], R[r][j], R[r + 1][j],
+                              R[r + 3][j], R[r + 4][j], win[0][r][j], win[1][r][j], win[3][r][j],
+                              win[4][r][j], Q[j]);
+            if (!rok[r]) continue;
+            if constexpr (S <= 3) {
+              TG *row = outG + ((int64_t)z * plane_g + row_g + r * pitch_g - x);
+              store_point<TG, TM, VEC>(row, pitch_g, N, ragged, edge, x, y, Gout);
+            } else {
+              // RK4 combine (Sec. 2.1): p' = p + dt q + dt^2/6 (G1 + G2 + G3),
+              //                         q' = q + dt/6 (G1 + 2 G2 + 2 G3 + G4)
+              TM pS[VEC], G2h[VEC];
+              load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(b2) + hoff, pS);
+              load_as<TG, TM, VEC>(reinterpret_cast<const TG *>(b2 + C::OFF_HG) +
+                                       (ly + 2) * BXG + lx0 + HXG, G2h);
+              TM pn[VEC], qn[VEC], pl[VEC], ql[VEC];
+#pragma unroll
+              for (int j = 0; j < VEC; ++j) {
+                const TM g1 = cur[0][j], g3 = cur[1][j];
+                const TM dp = fmaT(cf.b6, (g1 + G2h[j]) + g3, cf.a1 * qS[j]);
+                const TM dq = cf.d6 * ((g1 + Gout[j]) + (TM)2 * (G2h[j] + g3));
+                if constexpr (C::KAHAN) {
+                  two_sum(pS[j], dp + cur[2][j], pn[j], pl[j]);
+                  two_sum(qS[j], dq + cur[3][j], qn[j], ql[j]);
+                } else {
+                  pn[j] = pS[j] + dp;
+                  qn[j] = qS[j] + dq;
+                }
+                if (x + j < N) {
+                  const TM a = pn[j] < (TM)0 ? -pn[j] : pn[j];
+                  // NaN and overflow both read as +inf in the running max
+                  run_max = (a <= run_max) ? run_max : ((a == a) ? a : (TM)INFINITY);
+                }
+              }
+              const int64_t off = (int64_t)z * plane_s + row_s + r * pitch_s - x;
+              store_point<TS, TM, VEC>(outP + off, pitch_s, N, ragged, edge, x, y, pn);
+              store_point<TS, TM, VEC>(outQ + off, pitch_s, N, ragged, edge, x, y, qn);
+              if constexpr (C::KAHAN) {
+                store_point<TS, TM, VEC>(outPL + off, pitch_s, N, ragged, edge, x, y, pl);
+                store_point<TS, TM, VEC>(outQL + off, pitch_s, N, ragged, edge, x, y, ql);
+              }
+            }
+          }
+        }
+        // release the slots this warp no longer needs
+        __syncwarp();
+        if (lane == 0) {
+          if (m < 2 || m >= nplanes - 2) mbar_arrive(&empty[slot]);
+          if (m >= 4) mbar_arrive(&empty[s2]);
+        }
+        if (++slot == RING) { slot = 0; phase ^= 1u; }
+      }
+      if constexpr (S == 4) {
+        double v = (double)run_max;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) atomicMax(d->maxabs + prm.k, (unsigned long long)__double_as_longlong(v));
+      }
+    }
+  }
+};
+
+template <class C>
+__global__ void __launch_bounds__(C::THREADS, C::MINB)
+    stage_kernel(const StageParams prm) {
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-  Coef<TM> *coef = reinterpret_cast<Coef<TM> *>(smem + 128);
-  int *flags = reinterpret_cast<int *>(smem + 240);   // [0] skip item, [1] abort
-  static_assert(128 + sizeof(Coef<TM>) <= 240, "header layout");
-  TM *pplane[2] = {reinterpret_cast<TM *>(smem + C::HEADER),
-                   reinterpret_cast<TM *>(smem + C::HEADER + C::PPLANE_BYTES)};
-  unsigned char *ring = smem + C::HEADER + 2 * C::PPLANE_BYTES;
-  __shared__ double warp_max[32];
-
-  const int tid = threadIdx.x;
-  const int txt = tid % TPR, tyt = tid / TPR;
-  const int lx0 = txt * VEC;
-
-  if (tid == 0) {
-    for (int r = 0; r < RING; ++r) mbar_init(&bars[r], 1);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+  uint64_t *empty = reinterpret_cast<uint64_t *>(smem + 128);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 256);
+  unsigned char *ring = smem + C::HEADER;
+  static_assert(C::RING <= 16, "barrier area");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < C::RING; ++r) {
+      mbar_init(&full[r], 1);
+      mbar_init(&empty[r], C::NW);
+    }
+    *abort_flag = 0;
     fence_barrier_init();
   }
   __syncthreads();
-
-  uint32_t gplane = 0;  // planes consumed by this block so far (slot / phase bookkeeping)
-  const int nitems = *prm.nitems;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const WorkItem w = prm.items[it];
-    Desc *d = prm.descs + w.x;
-    // ---- per-item decisions and coefficients, by thread 0 (uniform via smem)
-    if (tid == 0) {
-      const long long n = d->n_base + prm.k;
-      int skip = (n >= d->n_end) || (d->stop_k <= prm.k);
-      if (S == 1 && !skip && prm.k > 0) {
-        const double m = __longlong_as_double((long long)d->maxabs[prm.k - 1]);
-        const bool nonfin = !(m <= 1.7976931348623157e308);
-        if (nonfin || (d->stop_thr > 0.0 && m > d->stop_thr)) {
-          atomicMin(&d->stop_k, (long long)prm.k);
-          skip = 1;
-        }
-      }
-      flags[0] = skip;
-      flags[1] = 0;
-      if (!skip) {
-        const double dt = d->dt;
-        const double tn = d->t0 + (double)n * dt;
-        const double ts = tn + (S == 1 ? 0.0 : (S == 4 ? dt : 0.5 * dt));
-        const double c = exp(-2.0 * ts) * d->inv_h2;
-        Coef<TM> cf;
-        cf.c43 = (TM)(4.0 / 3.0 * c);
-        cf.cm12 = (TM)(-c / 12.0);
-        cf.ccen = C::DIFF ? (TM)d->mu2 : (TM)(d->mu2 - 7.5 * c);
-        cf.nlam = (TM)(-d->lambda);
-        cf.m3 = (TM)(-3.0);
-        if (S == 2) { cf.a1 = (TM)(0.5 * dt); cf.a2 = (TM)0; }
-        if (S == 3) { cf.a1 = (TM)(0.5 * dt); cf.a2 = (TM)(0.25 * dt * dt); }
-        if (S == 4) { cf.a1 = (TM)dt; cf.a2 = (TM)(0.5 * dt * dt); }
-        if (S == 1) { cf.a1 = (TM)0; cf.a2 = (TM)0; }
-        cf.b6 = (TM)(dt * dt / 6.0);
-        cf.d6 = (TM)(dt / 6.0);
-        *coef = cf;
-        for (int t = 0; t < NUM_TMAPS; ++t) tmap_acquire(d->tmaps + t);
-      }
-    }
-    __syncthreads();
-    if (flags[0]) continue;
-    const Coef<TM> cf = *coef;
-    const int N = d->N;
-    const bool periodic = d->bc == 1;
-    const long long n = d->n_base + prm.k;
-    const int set = (int)(n & 1);
-    const int x0 = (w.y & 0xffff) * TX, y0 = (w.y >> 16) * TY;
-    const int z0 = w.z, len = w.w;
-    const int nplanes = len + 4;
-    const CUtensorMap *tm = d->tmaps;
-
-    // ---- TMA producer (thread 0): plane m of this item into its ring slot
-    auto issue = [&](int m) {
-      const uint32_t gp = gplane + (uint32_t)m;
-      const int slot = (int)(gp % RING);
-      uint64_t *bar = &bars[slot];
-      unsigned char *base = ring + slot * C::SLOT_BYTES;
-      int z = z0 - 2 + m;
-      if (periodic) z = (z % N + N) % N;
-      fence_proxy_async();
-      mbar_expect_tx(bar, C::TX_BYTES);
-      tma_load_3d(base, tm + (set ? TM_P_H1 : TM_P_H0), bar, x0, y0, z);
-      if constexpr (C::NHS == 2)
-        tma_load_3d(base + C::HS_BYTES, tm + (set ? TM_Q_H1 : TM_Q_H0), bar, x0, y0, z);
-      if constexpr (C::NHG == 1)
-        tma_load_3d(base + C::OFF_HG, tm + (S == 3 ? TM_G1_H : TM_G2_H), bar, x0, y0, z);
-      if constexpr (S == 1)
-        tma_load_3d(base + C::OFF_IS, tm + (set ? TM_Q_I1 : TM_Q_I0), bar, x0 + HXS, y0 + 2, z);
-      if constexpr (S == 4 && C::KAHAN) {
-        tma_load_3d(base + C::OFF_IS, tm + (set ? TM_PLO_I1 : TM_PLO_I0), bar, x0 + HXS, y0 + 2, z);
-        tma_load_3d(base + C::OFF_IS + C::IS_BYTES, tm + (set ? TM_QLO_I1 : TM_QLO_I0), bar,
-                    x0 + HXS, y0 + 2, z);
-      }
-      if constexpr (S == 2)
-        tma_load_3d(base + C::OFF_IG, tm + TM_G1_I, bar, x0 + HXG, y0 + 2, z);
-      if constexpr (S == 3)
-        tma_load_3d(base + C::OFF_IG, tm + TM_G2_I, bar, x0 + HXG, y0 + 2, z);
-      if constexpr (S == 4) {
-        tma_load_3d(base + C::OFF_IG, tm + TM_G1_I, bar, x0 + HXG, y0 + 2, z);
-        tma_load_3d(base + C::OFF_IG + C::IG_BYTES, tm + TM_G3_I, bar, x0 + HXG, y0 + 2, z);
-      }
-    };
-    // P = stage argument at halo-tile position (row, col of the state tiles)
-    auto combine_at = [&](const unsigned char *base, int lx, int ly, TM (&out)[VEC]) {
-      const TS *hp = reinterpret_cast<const TS *>(base);
-      load_as<TS, TM, VEC>(hp + (ly + 2) * BXS + lx + HXS, out);
-      if constexpr (S >= 2) {
-        TM qv[VEC];
-        const TS *hq = reinterpret_cast<const TS *>(base + C::HS_BYTES);
-        load_as<TS, TM, VEC>(hq + (ly + 2) * BXS + lx + HXS, qv);
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) out[j] = fmaT(cf.a1, qv[j], out[j]);
-      }
-      if constexpr (S >= 3) {
-        TM gv[VEC];
-        const TG *hg = reinterpret_cast<const TG *>(base + C::OFF_HG);
-        load_as<TG, TM, VEC>(hg + (ly + 2) * BXG + lx + HXG, gv);
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) out[j] = fmaT(cf.a2, gv[j], out[j]);
-      }
-    };
-
-    int issued = cmin(RING, nplanes);
-    if (tid == 0)
-      for (int m = 0; m < issued; ++m) issue(m);
-
-    TM win[5][VEC];
-#pragma unroll
-    for (int a = 0; a < 5; ++a)
-#pragma unroll
-      for (int j = 0; j < VEC; ++j) win[a][j] = (TM)0;
-    TM run_max = (TM)0;
-    bool aborted = false;
-
-    int consumed = 0;
-    for (int m = 0; m < nplanes; ++m) {
-      const uint32_t gp = gplane + (uint32_t)m;
-      consumed = m + 1;
-      const int slot = (int)(gp % RING);
-      if (!mbar_wait_bounded(&bars[slot], (gp / RING) & 1u)) {
-        flags[1] = 1;
-        atomicOr(prm.err, (unsigned)DEV_ERR_TIMEOUT);
-      }
-      const unsigned char *base = ring + slot * C::SLOT_BYTES;
-      // own column: P at plane z0-2+m enters the window
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) win[a][j] = win[a + 1][j];
-      combine_at(base, lx0, tyt, win[4]);
-      const bool out = m >= 4;
-      // slot of the output plane z0 + m - 4 (loaded as plane m - 2)
-      const unsigned char *obase = ring + (int)((gp + (uint32_t)(2 * RING - 2)) % RING) * C::SLOT_BYTES;
-      TM *pp = pplane[m & 1];
-      if (out) {
-        VecIO<TM>::store(pp + (tyt + 2) * BXM + HXM + lx0, win[2]);
-        for (int hix = tid; hix < C::NHALO; hix += C::THREADS) {
-          int lx, ly;
-          if (hix < 4 * TPR) {
-            const int r = hix / TPR;
-            ly = (r < 2) ? r - 2 : TY + (r - 2);
-            lx = (hix % TPR) * VEC;
-          } else {
-            const int h2 = hix - 4 * TPR;
-            ly = h2 % TY;
-            lx = (h2 / TY) ? TX : -VEC;
-          }
-          TM v[VEC];
-          combine_at(obase, lx, ly, v);
-          VecIO<TM>::store(pp + (ly + 2) * BXM + HXM + lx, v);
-        }
-      }
-      __syncthreads();
-      if (flags[1]) { aborted = true; break; }
-      if (tid == 0 && m >= 3) {
-        const int pn = m - 3 + RING;
-        if (pn < nplanes) { issue(pn); issued = pn + 1; }
-      }
-      if (!out) continue;
-
-      // ---- stencil at plane z = z0 + m - 4 for the thread's VEC points
-      const int z = z0 + m - 4;
-      const int x = x0 + lx0, y = y0 + tyt;
-      const TM *prow = pp + (tyt + 2) * BXM + HXM + lx0;
-      TM E[3 * VEC];
-      {
-        TM a[VEC], c[VEC];
-        VecIO<TM>::load(prow - VEC, a);
-        VecIO<TM>::load(prow + VEC, c);
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) { E[j] = a[j]; E[VEC + j] = win[2][j]; E[2 * VEC + j] = c[j]; }
-      }
-      TM ym1[VEC], yp1[VEC], ym2[VEC], yp2[VEC];
-      VecIO<TM>::load(prow - BXM, ym1);
-      VecIO<TM>::load(prow + BXM, yp1);
-      VecIO<TM>::load(prow - 2 * BXM, ym2);
-      VecIO<TM>::load(prow + 2 * BXM, yp2);
-
-      // pointwise inputs at the output plane
-      TM Q[VEC], Gint0[VEC], Gint1[VEC], pS[VEC], qS[VEC], loP[VEC], loQ[VEC];
-      {
-        const TS *hp = reinterpret_cast<const TS *>(obase);
-        const int hoff = (tyt + 2) * BXS + lx0 + HXS;
-        if constexpr (S == 1) {
-          load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(obase + C::OFF_IS) + tyt * TX + lx0, Q);
-        } else {
-          load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(obase + C::HS_BYTES) + hoff, qS);
-          const TG *ig = reinterpret_cast<const TG *>(obase + C::OFF_IG) + tyt * TX + lx0;
-          load_as<TG, TM, VEC>(ig, Gint0);   // S2: G1, S3: G2, S4: G1
-          if constexpr (S == 4) load_as<TG, TM, VEC>(ig + C::IG_BYTES / (int)sizeof(TG), Gint1);  // G3
-          if constexpr (S == 2 || S == 3) {  // q + dt/2 G1 (S2), q + dt/2 G2 (S3)
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) Q[j] = fmaT(cf.a1, Gint0[j], qS[j]);
-          }
-          if constexpr (S == 4) {
-            load_as<TS, TM, VEC>(hp + hoff, pS);
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) Q[j] = fmaT(cf.a1, Gint1[j], qS[j]);  // q + dt G3
-            if constexpr (C::KAHAN) {
-              const TS *is = reinterpret_cast<const TS *>(obase + C::OFF_IS) + tyt * TX + lx0;
-              load_as<TS, TM, VEC>(is, loP);
-              load_as<TS, TM, VEC>(is + C::IS_BYTES / (int)sizeof(TS), loQ);
-            }
-          }
-        }
-      }
-      TM Gout[VEC];
-#pragma unroll
-      for (int j = 0; j < VEC; ++j) {
-        const TM P0 = E[VEC + j];
-        TM s1, s2;
-        if constexpr (C::DIFF) {
-          s1 = ((E[VEC + j - 1] - P0) + (E[VEC + j + 1] - P0)) +
-               (((ym1[j] - P0) + (yp1[j] - P0)) + ((win[1][j] - P0) + (win[3][j] - P0)));
-          s2 = ((E[VEC + j - 2] - P0) + (E[VEC + j + 2] - P0)) +
-               (((ym2[j] - P0) + (yp2[j] - P0)) + ((win[0][j] - P0) + (win[4][j] - P0)));
-        } else {
-          s1 = ((E[VEC + j - 1] + E[VEC + j + 1]) + (ym1[j] + yp1[j])) + (win[1][j] + win[3][j]);
-          s2 = ((E[VEC + j - 2] + E[VEC + j + 2]) + (ym2[j] + yp2[j])) + (win[0][j] + win[4][j]);
-        }
-        TM g = fmaT(cf.nlam * (P0 * P0), P0, cf.m3 * Q[j]);
-        g = fmaT(cf.ccen, P0, g);
-        g = fmaT(cf.cm12, s2, g);
-        Gout[j] = fmaT(cf.c43, s1, g);
-      }
-
-      const bool yok = y < N;
-      if constexpr (S <= 3) {
-        if (yok && x < N) {
-          TG *gbase = reinterpret_cast<TG *>(d->f[S == 1 ? F_G1 : (S == 2 ? F_G2 : F_G3)]);
-          store_point<TG, TM, VEC>(gbase, d->pitch_g, d->plane_g, HXG, N, periodic, x, y, z, Gout);
-        }
-      } else {
-        // RK4 combine (Sec. 2.1): p' = p + dt q + dt^2/6 (G1 + G2 + G3),
-        //                         q' = q + dt/6 (G1 + 2 G2 + 2 G3 + G4)
-        TM G2v[VEC];
-        {
-          const TG *hg = reinterpret_cast<const TG *>(obase + C::OFF_HG);
-          load_as<TG, TM, VEC>(hg + (tyt + 2) * BXG + lx0 + HXG, G2v);
-        }
-        TM pn[VEC], qn[VEC], pl[VEC], ql[VEC];
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-          const TM dp = fmaT(cf.b6, (Gint0[j] + G2v[j]) + Gint1[j], cf.a1 * qS[j]);
-          const TM dq = cf.d6 * ((Gint0[j] + Gout[j]) + (TM)2 * (G2v[j] + Gint1[j]));
-          if constexpr (C::KAHAN) {
-            two_sum(pS[j], dp + loP[j], pn[j], pl[j]);
-            two_sum(qS[j], dq + loQ[j], qn[j], ql[j]);
-          } else {
-            pn[j] = pS[j] + dp;
-            qn[j] = qS[j] + dq;
-          }
-        }
-        if (yok && x < N) {
-          const int so = set ? 0 : 1;  // write the other buffer set
-          store_point<TS, TM, VEC>(reinterpret_cast<TS *>(d->f[F_P0 + so]), d->pitch_s,
-                                   d->plane_s, HXS, N, periodic, x, y, z, pn);
-          store_point<TS, TM, VEC>(reinterpret_cast<TS *>(d->f[F_Q0 + so]), d->pitch_s,
-                                   d->plane_s, HXS, N, periodic, x, y, z, qn);
-          if constexpr (C::KAHAN) {
-            store_point<TS, TM, VEC>(reinterpret_cast<TS *>(d->f[F_PLO0 + so]), d->pitch_s,
-                                     d->plane_s, HXS, N, periodic, x, y, z, pl);
-            store_point<TS, TM, VEC>(reinterpret_cast<TS *>(d->f[F_QLO0 + so]), d->pitch_s,
-                                     d->plane_s, HXS, N, periodic, x, y, z, ql);
-          }
-#pragma unroll
-          for (int j = 0; j < VEC; ++j) {
-            if (x + j < N) {
-              const TM a = pn[j] < (TM)0 ? -pn[j] : pn[j];
-              // NaN and overflow both read as +inf in the running max
-              run_max = (a <= run_max) ? run_max : ((a == a) ? a : (TM)INFINITY);
-            }
-          }
-        }
-      }
-    }
-    if (aborted) {
-      // let the copies already in flight land before the block exits
-      if (tid == 0) {
-        for (int m2 = consumed; m2 < issued; ++m2) {
-          const uint32_t gp2 = gplane + (uint32_t)m2;
-          (void)mbar_wait_bounded(&bars[gp2 % RING], (gp2 / RING) & 1u);
-        }
-      }
-      return;
-    }
-    gplane += (uint32_t)nplanes;
-    if constexpr (S == 4) {
-      // block max of |p'| -> one atomicMax on the double bit pattern (non-negative)
-      double v = (double)run_max;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-      if ((tid & 31) == 0) warp_max[tid >> 5] = v;
-      __syncthreads();
-      if (tid == 0) {
-        double mx = 0.0;
-        for (int wi = 0; wi < (C::THREADS + 31) / 32; ++wi) mx = fmax(mx, warp_max[wi]);
-        atomicMax(d->maxabs + prm.k, (unsigned long long)__double_as_longlong(mx));
-      }
-    }
+  if (warp == C::NW) {
+    if (lane == 0) produce<C>(prm, full, empty, ring, abort_flag);
+  } else {
+    Consumer<C>::run(prm, full, empty, ring, abort_flag, warp, lane);
   }
 }
 

@@ -7,15 +7,15 @@ namespace {
 template <class C>
 KernelInfo info() {
   return KernelInfo{reinterpret_cast<const void *>(&stage_kernel<C>), C::THREADS, C::SMEM, C::RING,
-                    C::TX, C::TY};
+                    C::TX, C::TY, C::VEC, C::VY, C::NW};
 }
-template <class PR, int TX, int TY, int B>
+template <class PR, int V, int VY, int NW, int B, int MB>
 void add(VariantTable &t) {
   KernelInfo *k = t.k[t.count++];
-  k[0] = info<StageCfg<PR, TX, TY, B, 1>>();
-  k[1] = info<StageCfg<PR, TX, TY, B, 2>>();
-  k[2] = info<StageCfg<PR, TX, TY, B, 3>>();
-  k[3] = info<StageCfg<PR, TX, TY, B, 4>>();
+  k[0] = info<StageCfg<PR, V, VY, NW, B, MB, 1>>();
+  k[1] = info<StageCfg<PR, V, VY, NW, B, MB, 2>>();
+  k[2] = info<StageCfg<PR, V, VY, NW, B, MB, 3>>();
+  k[3] = info<StageCfg<PR, V, VY, NW, B, MB, 4>>();
 }
 }  // namespace
 
@@ -23,10 +23,11 @@ const VariantTable &variants_fp32_plain() {
   static const VariantTable table = [] {
     using PR = PrecFP32Plain;
     VariantTable t{};
-    add<PR, 32, 16, 110 * 1024>(t);   // 128 threads, 2 blocks / SM
-    add<PR, 32, 8, 55 * 1024>(t);     //  64 threads, 4 blocks / SM
-    add<PR, 64, 8, 110 * 1024>(t);    // 128 threads, 2 blocks / SM
-    add<PR, 64, 16, 220 * 1024>(t);   // 256 threads, 1 block / SM
+    // <precision, x points per lane, rows per warp, consumer warps, smem budget, min blocks/SM>
+    add<PR, 2, 1, 8, 110 * 1024, 2>(t);  // 64 x 8 tile, 9 warps
+    add<PR, 2, 2, 8, 220 * 1024, 1>(t);  // 64 x 16 tile, 9 warps
+    add<PR, 2, 2, 4, 110 * 1024, 2>(t);  // 64 x 8 tile, 5 warps
+    add<PR, 1, 2, 8, 110 * 1024, 2>(t);  // 32 x 16 tile, 9 warps
     return t;
   }();
   return table;

@@ -9,6 +9,9 @@ struct KernelInfo {
   int smem;         // dynamic shared memory bytes
   int ring;         // z-planes in the TMA ring
   int tx, ty;       // tile in x and y
+  int vec;          // consecutive x points per lane
+  int vy;           // rows per consumer warp
+  int nw;           // consumer warps
 };
 
 constexpr int kMaxVariants = 4;

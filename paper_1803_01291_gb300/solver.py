@@ -47,7 +47,8 @@ def variants(prec: int) -> List[dict]:
     for v in range(lib.hbe_variant_count(prec)):
         info = _lib.HbeVariant()
         _check(lib, lib.hbe_variant_info(prec, v, ctypes.byref(info)))
-        out.append(dict(tile_x=info.tile_x, tile_y=info.tile_y, threads=info.threads,
+        out.append(dict(tile_x=info.tile_x, tile_y=info.tile_y, threads=info.threads, vec=info.vec,
+                        rows_per_warp=info.rows_per_warp, consumer_warps=info.consumer_warps,
                         smem=list(info.smem_bytes), ring=list(info.ring)))
     return out
 
@@ -131,6 +132,21 @@ class Solver:
         assert a.shape == (self.N,) * 3 and b.shape == (self.N,) * 3
         dp = ctypes.POINTER(ctypes.c_double)
         self._chk(self.lib.hbe_set_initial(self._ctx, a.ctypes.data_as(dp), b.ctypes.data_as(dp), t0))
+
+    def set_initial_bumps(self, bumps0, bumps1=(), t0: float = 0.0):
+        """Initial data as sums of bumps A exp(-1/(1 - r^2/R^2)) evaluated on the
+        device; bumps0 / bumps1: sequences of (A, R, (cx, cy, cz))."""
+        def pack(bs):
+            A = np.array([b[0] for b in bs], dtype=np.float64)
+            R = np.array([b[1] for b in bs], dtype=np.float64)
+            c = np.array([list(b[2]) for b in bs], dtype=np.float64).reshape(-1)
+            return A, R, c
+        dp = ctypes.POINTER(ctypes.c_double)
+        A0, R0, c0 = pack(list(bumps0))
+        A1, R1, c1 = pack(list(bumps1))
+        ptr = lambda a: a.ctypes.data_as(dp) if a.size else None
+        self._chk(self.lib.hbe_set_initial_bumps(self._ctx, len(A0), ptr(A0), ptr(R0), ptr(c0),
+                                                 len(A1), ptr(A1), ptr(R1), ptr(c1), t0))
 
     def step(self, nsteps: int, dt: float) -> int:
         """Advance nsteps RK4 steps; returns OK, STOPPED or NONFINITE."""

@@ -1,0 +1,70 @@
+"""Continuous-batching server: every request completes, memory admission is
+respected, and each result equals the same problem solved alone (bitwise)."""
+import numpy as np
+import pytest
+
+import __graft_entry__  # noqa: F401
+import hbe_inputs as hi
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hbe():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1803_01291_gb300 as m
+    return m
+
+
+def small_stream(count, seed):
+    reqs = hi.request_stream(count, seed=seed, rate=200.0, sizes=(32, 48, 64))
+    for r in reqs:
+        r.T = min(r.T, 0.6)  # short horizons keep the test quick
+    return reqs
+
+
+def test_bump_initial_data_matches_host_generator(hbe):
+    r = small_stream(1, 5)[0]
+    phi0, _ = r.initial()
+    for prec, tol in ((hbe.FP64, 4e-16), (hbe.FP32, 0.0)):
+        with hbe.Solver(r.N, r.L, r.mu, r.lam, 0, prec) as s:
+            s.set_initial_bumps(r.bumps)
+            a = s.read()[0]
+        ref = phi0 if prec == hbe.FP64 else phi0.astype(np.float32).astype(np.float64)
+        if prec == hbe.FP32:
+            # hi + lo pair holds the double to ~2^-48 relative
+            assert np.max(np.abs(a - phi0)) <= 1e-14 * max(1.0, np.max(np.abs(phi0)))
+        else:
+            assert np.max(np.abs(a - ref)) <= tol * max(1.0, np.max(np.abs(ref))) * 8
+
+
+@pytest.mark.parametrize("realtime", [False, True])
+def test_server_completes_and_matches_alone(hbe, realtime):
+    from paper_1803_01291_gb300 import serve
+    reqs = serve.requests_from_stream(small_stream(10, 7))
+    budget = 3 * hbe.workspace_bytes(64, 0, hbe.FP32)
+    srv = serve.Server(hbe.FP32, K=4, hbm_budget=budget)
+    stats = srv.run(reqs, realtime=realtime)
+    srv.close()
+    assert len(stats.results) == len(reqs)
+    assert stats.peak_bytes <= budget
+    assert stats.peak_members >= 1
+    summ = stats.summary()
+    assert summ["p99_latency_s"] >= summ["p50_latency_s"] >= 0
+    by_id = {r.rid: r for r in stats.results}
+    for q in reqs:
+        res = by_id[q.rid]
+        assert res.steps == q.nsteps
+        with hbe.Solver(q.N, q.L, q.mu, q.lam, 0, hbe.FP32) as s:
+            s.set_initial_bumps(q.bumps)
+            s.step(q.nsteps, q.dt)
+            assert s.diag()["max_abs_phi"] == res.max_abs_phi
+
+
+def test_alone_baseline_runs(hbe):
+    from paper_1803_01291_gb300 import serve
+    reqs = serve.requests_from_stream(small_stream(3, 9))
+    out = serve.run_alone(reqs, hbe.FP64)
+    assert out["requests"] == 3 and out["gpoint_steps_per_s"] > 0
