@@ -183,6 +183,32 @@ const char *hbe_status_string(int status);
 /* Number of stage-kernel launches this context (or batch) has enqueued. */
 int64_t hbe_launch_count(const hbe_ctx *ctx);
 
+/* ---- Stepping without device allocation -------------------------------- */
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory at the moment they step a problem: code that
+ * runs while another library is capturing a CUDA graph on its stream (an
+ * allocation there would break or serialise the capture), runtimes that own
+ * all device memory through their own pool and forbid other allocations, and
+ * real-time loops where cudaMalloc may block or fail under memory pressure.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  The caller
+ * passes the initial fields d_phi0, d_phi1 and the result fields d_phi, d_psi
+ * (device arrays of N^3 doubles, x fastest); every intermediate array (padded
+ * state, stage values, kernel descriptors) lives in one fixed __device__
+ * array inside libhbe of about 7.3 MB, which every GPU that loads the library
+ * holds until the process exits.  FP64 arithmetic; N in [8, 48], and a larger
+ * N returns HBE_EINVAL because the array holds nothing bigger.  Grid,
+ * boundary and time conventions as for hbe_create / hbe_step: nsteps RK4
+ * steps of size dt from time t0.  The first call on a device looks up the
+ * array's device address with that device current, so make that first call
+ * before any stream capture.  All calls share the one array (each clears what
+ * must start at zero), so calls that overlap on the GPU race.  Runs on
+ * `stream` (cudaStream_t, NULL = legacy default) and blocks until done;
+ * returns HBE_ETIMEOUT if a kernel's bounded wait expired. */
+hbe_status hbe_step_fp64_noalloc(int N, double L, double mu, double lambda, int bc,
+                                 const double *d_phi0, const double *d_phi1, double t0,
+                                 double dt, int64_t nsteps, double *d_phi, double *d_psi,
+                                 void *stream);
+
 /* ---- Batched stepping (continuous batching) ---------------------------- */
 /* A batch advances many contexts of one precision together: every RK4 stage
  * is one persistent kernel launch over the tiles of all members, and K steps
