@@ -156,6 +156,7 @@ def dist_setup(gpus: int):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world != gpus and world != 1:
         raise SystemExit(f"--gpus {gpus} but WORLD_SIZE={world}")
+    # torchrun sets the rendezvous; a bare run is rank 0 of 1
     return rank, world, local
 
 
@@ -172,6 +173,12 @@ def max_over_ranks(value: float, world, torch, device):
     t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(units_per_rank: float, secs_max: float, world: int) -> float:
+    """Whole-job throughput in units of 1e9 per second: every rank's units over
+    the slowest rank's time (weak scaling: each rank solves its own replica)."""
+    return units_per_rank * world / secs_max / 1e9
 
 
 def workload(N: int):
@@ -376,8 +383,7 @@ def main():
         secs, stage_ms, launches = time_path(hbe, torch, prob, hbe.FP32, args.steps, args.warmup)
     secs = max_over_ranks(secs, world, torch, device)
     barrier(world, torch)
-    pts = float(N) ** 3 * args.steps * world
-    value = pts / secs / 1e9
+    value = aggregate(float(N) ** 3 * args.steps, secs, world)
 
     sb = stage_bytes("fp32")
     stage_gbs = [sb[i] * N ** 3 / (stage_ms[i] / 1e3) / 1e9 for i in range(4)]

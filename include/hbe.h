@@ -81,7 +81,7 @@ typedef struct {
 typedef struct {
   int32_t tile_x, tile_y;   /* x-y tile of one thread block */
   int32_t threads;          /* threads per block: 32 * (consumer_warps + 1 producer warp) */
-  int32_t vec;              /* consecutive x points per lane (tile_x = 32 * vec) */
+  int32_t vec;              /* consecutive x points per lane, 1, 2 or 4 (tile_x = 32 * vec) */
   int32_t rows_per_warp;    /* tile rows per consumer warp (tile_y = consumer_warps * rows) */
   int32_t consumer_warps;
   int32_t smem_bytes[4];    /* dynamic shared memory per stage kernel */

@@ -82,12 +82,15 @@ struct StageCfg {
   static constexpr int HXG = 16 / (int)sizeof(TG);
   static constexpr int BY = TY + 4;
   static constexpr int BXS = TX + 2 * HXS, BXG = TX + 2 * HXG;
-  // ring slot composition: halo tiles of the fields that enter the stencil, then
+  // S = 1..4: one RK stage per launch; S = 5: stages 1 and 2 in one launch;
+  // S = 6: stages 3 and 4 (with the RK4 combine) in one launch.
+  static constexpr bool PAIR = S >= 5;
+  // ring slot composition: halo tiles of the fields that enter a stencil, then
   // interior tiles of the fields read at the point only
-  static constexpr int NHS = (S == 1) ? 1 : 2;                           // p [, q]
-  static constexpr int NHG = (S >= 3) ? 1 : 0;                           // G1 (S3) / G2 (S4)
-  static constexpr int NIS = (S == 1) ? 1 : ((S == 4 && KAHAN) ? 2 : 0); // q (S1) / plo, qlo (S4)
-  static constexpr int NIG = (S == 1) ? 0 : ((S == 4) ? 2 : 1);          // G1 | G2 | G1, G3
+  static constexpr int NHS = (S == 1) ? 1 : 2;                                  // p [, q]
+  static constexpr int NHG = (S == 3 || S == 4) ? 1 : (S == 6 ? 2 : 0);         // G1 | G2 | G1, G2
+  static constexpr int NIS = (S == 1) ? 1 : (((S == 4 || S == 6) && KAHAN) ? 2 : 0);
+  static constexpr int NIG = (S == 1 || S >= 5) ? 0 : ((S == 4) ? 2 : 1);       // G1 | G2 | G1, G3
   static constexpr int HS_RAW = BY * BXS * (int)sizeof(TS);
   static constexpr int HG_RAW = BY * BXG * (int)sizeof(TG);
   static constexpr int IS_RAW = TY * TX * (int)sizeof(TS);
@@ -104,7 +107,7 @@ struct StageCfg {
   static constexpr int RING = cmax(4, cmin(16, (BUDGET_ - HEADER) / SLOT_BYTES));
   static constexpr int SMEM = HEADER + RING * SLOT_BYTES;
   static constexpr int MINB = MINB_;  // blocks per SM the registers must allow
-  static_assert(VEC == 1 || VEC == 2, "one or two x points per lane");
+  static_assert(VEC == 1 || VEC == 2 || VEC == 4, "1, 2 or 4 x points per lane");
   static_assert(VEC * (int)sizeof(TM) <= 16, "lane vector of <= 16 bytes");
   static_assert(HXS >= 2 && HXG >= 2 && HXS % VEC == 0 && HXG % VEC == 0, "halo alignment");
   static_assert(BXG <= 256 && BXS <= 256 && BY <= 256, "TMA box limit");
@@ -268,7 +271,7 @@ template <int S>
 __device__ __forceinline__ bool item_active(Desc *d, int k, bool leader) {
   const long long n = d->n_base + k;
   if (n >= d->n_end || __ldcg(&d->stop_k) <= k) return false;
-  if (S == 1 && k > 0) {
+  if ((S == 1 || S == 5) && k > 0) {
     const double m = __longlong_as_double((long long)__ldcg(d->maxabs + k - 1));
     if (!(m <= 1.7976931348623157e308) || (d->stop_thr > 0.0 && m > d->stop_thr)) {
       if (leader) atomicMin(&d->stop_k, (long long)k);
@@ -346,10 +349,18 @@ __device__ __forceinline__ void produce(const StageParams &prm, uint64_t *full, 
       mbar_expect_tx(bar, C::TX_BYTES);
       tma_load_3d(base, mp, bar, x0, y0, z);
       if constexpr (C::NHS == 2) tma_load_3d(base + C::HS_BYTES, mq, bar, x0, y0, z);
-      if constexpr (C::NHG == 1) tma_load_3d(base + C::OFF_HG, mg, bar, x0, y0, z);
+      if constexpr (C::NHG == 1 && !C::PAIR) tma_load_3d(base + C::OFF_HG, mg, bar, x0, y0, z);
       constexpr int HXS = C::HXS, HXG = C::HXG;
+      if constexpr (S == 6) {
+        tma_load_3d(base + C::OFF_HG, tm + TM_G1_H, bar, x0, y0, z);
+        tma_load_3d(base + C::OFF_HG + C::HG_BYTES, tm + TM_G2_H, bar, x0, y0, z);
+        if constexpr (C::KAHAN) {
+          tma_load_3d(base + C::OFF_IS, mlp, bar, x0 + HXS, y0 + 2, z);
+          tma_load_3d(base + C::OFF_IS + C::IS_BYTES, mlq, bar, x0 + HXS, y0 + 2, z);
+        }
+      }
       if constexpr (S == 1) tma_load_3d(base + C::OFF_IS, mi0, bar, x0 + HXS, y0 + 2, z);
-      if constexpr (S >= 2) tma_load_3d(base + C::OFF_IG, mi0, bar, x0 + HXG, y0 + 2, z);
+      if constexpr (S >= 2 && S <= 4) tma_load_3d(base + C::OFF_IG, mi0, bar, x0 + HXG, y0 + 2, z);
       if constexpr (S == 4) {
         tma_load_3d(base + C::OFF_IG + C::IG_BYTES, mi1, bar, x0 + HXG, y0 + 2, z);
         if constexpr (C::KAHAN) {
@@ -384,22 +395,28 @@ struct Consumer {
   static constexpr int BXS = C::BXS, BXG = C::BXG, HXS = C::HXS, HXG = C::HXG;
   static constexpr int NI = C::NIS + C::NIG;  // point-only input fields
 
-  // Stage argument P at tile position (lx, ly) (ly in [-2, TY+2)) from the ring tiles.
-  static __device__ __forceinline__ void comb(const unsigned char *base, const Coef<TM> &cf,
-                                              int lx, int ly, TM (&out)[VEC]) {
-    load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(base) + (ly + 2) * BXS + lx + HXS, out);
+  // Stage argument P at n consecutive tile positions from (lx, ly) (ly in
+  // [-2, TY+2)), formed from the ring tiles.
+  template <int n>
+  static __device__ __forceinline__ void comb_n(const unsigned char *base, const Coef<TM> &cf,
+                                                int lx, int ly, TM (&out)[n]) {
+    load_as<TS, TM, n>(reinterpret_cast<const TS *>(base) + (ly + 2) * BXS + lx + HXS, out);
     if constexpr (S >= 2) {
-      TM qv[VEC];
-      load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(base + C::HS_BYTES) + (ly + 2) * BXS + lx + HXS, qv);
+      TM qv[n];
+      load_as<TS, TM, n>(reinterpret_cast<const TS *>(base + C::HS_BYTES) + (ly + 2) * BXS + lx + HXS, qv);
 #pragma unroll
-      for (int j = 0; j < VEC; ++j) out[j] = fmaT(cf.a1, qv[j], out[j]);
+      for (int j = 0; j < n; ++j) out[j] = fmaT(cf.a1, qv[j], out[j]);
     }
     if constexpr (S >= 3) {
-      TM gv[VEC];
-      load_as<TG, TM, VEC>(reinterpret_cast<const TG *>(base + C::OFF_HG) + (ly + 2) * BXG + lx + HXG, gv);
+      TM gv[n];
+      load_as<TG, TM, n>(reinterpret_cast<const TG *>(base + C::OFF_HG) + (ly + 2) * BXG + lx + HXG, gv);
 #pragma unroll
-      for (int j = 0; j < VEC; ++j) out[j] = fmaT(cf.a2, gv[j], out[j]);
+      for (int j = 0; j < n; ++j) out[j] = fmaT(cf.a2, gv[j], out[j]);
     }
+  }
+  static __device__ __forceinline__ void comb(const unsigned char *base, const Coef<TM> &cf,
+                                              int lx, int ly, TM (&out)[VEC]) {
+    comb_n<VEC>(base, cf, lx, ly, out);
   }
 
   // x neighbours (x-2, x-1, x+1, x+2) of the lane's VEC points in tile row ly,
@@ -411,7 +428,16 @@ struct Consumer {
     if constexpr (S == 1) {
       // P = p: read the neighbours straight from the halo tile
       const TS *hp = reinterpret_cast<const TS *>(base) + (ly + 2) * BXS + lx0 + HXS;
-      if constexpr (VEC == 2) {
+      if constexpr (VEC == 4) {
+        TM a[4], b[4];
+        load_as<TS, TM, 4>(hp - 4, a);
+        load_as<TS, TM, 4>(hp + 4, b);
+        const TM e[8] = {a[2], a[3], c[0], c[1], c[2], c[3], b[0], b[1]};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          m2[j] = e[j]; m1[j] = e[j + 1]; p1[j] = e[j + 3]; p2[j] = e[j + 4];
+        }
+      } else if constexpr (VEC == 2) {
         TM a[2], b[2];
         load_as<TS, TM, 2>(hp - 2, a);
         load_as<TS, TM, 2>(hp + 2, b);
@@ -419,6 +445,25 @@ struct Consumer {
         m2[1] = a[1]; m1[1] = c[0]; p1[1] = b[0]; p2[1] = b[1];
       } else {
         m2[0] = (TM)hp[-2]; m1[0] = (TM)hp[-1]; p1[0] = (TM)hp[1]; p2[0] = (TM)hp[2];
+      }
+    } else if constexpr (VEC == 4) {
+      // the two points each side come from the neighbouring lanes, or from the
+      // halo columns for the first and last lane
+      TM pc = shfl_up1(c[2], 1), pd = shfl_up1(c[3], 1);
+      TM na = shfl_dn1(c[0], 1), nb = shfl_dn1(c[1], 1);
+      if (lane == 0) {
+        TM hv[2];
+        Consumer::template comb_n<2>(base, cf, -2, ly, hv);
+        pc = hv[0]; pd = hv[1];
+      } else if (lane == 31) {
+        TM hv[2];
+        Consumer::template comb_n<2>(base, cf, TX, ly, hv);
+        na = hv[0]; nb = hv[1];
+      }
+      const TM e[8] = {pc, pd, c[0], c[1], c[2], c[3], na, nb};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        m2[j] = e[j]; m1[j] = e[j + 1]; p1[j] = e[j + 3]; p2[j] = e[j + 4];
       }
     } else if constexpr (VEC == 2) {
       TM pa = shfl_up1(c[0], 1), pb = shfl_up1(c[1], 1);
@@ -495,8 +540,9 @@ struct Consumer {
       const int x0 = (w.y & 0xffff) * TX, y0 = (w.y >> 16) * C::TY;
       const int z0 = w.z, len = w.w, nplanes = len + 4;
       const bool ragged = x0 + TX > N;
-      const bool edge = periodic && (x0 < 2 || x0 + TX > N - 2 || y0 < 2 || y0 + C::TY > N - 2);
       const int x = x0 + lx0;
+      // periodic ghost copies are written only by the lanes / rows next to a wrap
+      const bool lane_edge = periodic && (x < 2 || x + VEC > N - 2);
       const int64_t pitch_s = d->pitch_s, plane_s = d->plane_s;
       const int64_t pitch_g = d->pitch_g, plane_g = d->plane_g;
       const int64_t row_s = (int64_t)(y0 + ly0 + 2) * pitch_s + HXS + x;  // row r: + r pitch
@@ -601,6 +647,7 @@ struct Consumer {
                               R[r + 3][j], R[r + 4][j], win[0][r][j], win[1][r][j], win[3][r][j],
                               win[4][r][j], Q[j]);
             if (!rok[r]) continue;
+            const bool edge = lane_edge || (periodic && (y < 2 || y >= N - 2));
             if constexpr (S <= 3) {
               TG *row = outG + ((int64_t)z * plane_g + row_g + r * pitch_g - x);
               store_point<TG, TM, VEC>(row, pitch_g, N, ragged, edge, x, y, Gout);
@@ -658,6 +705,327 @@ struct Consumer {
   }
 };
 
+// Coefficients of a fused pair of stages, formed in double precision.
+template <class TM>
+struct PairCoef {
+  TM c43a, cm12a, ccena;  // stencil coefficients of the first stage of the pair
+  TM c43b, cm12b, ccenb;  // and of the second
+  TM nlam, m3;
+  TM aq, ag;              // Pa = p + aq q + ag G1          (pair 3+4)
+  TM bq, bg;              // Pb = p + bq q + bg G2          (pair 1+2: bg = 0)
+  TM qa;                  // Qa = q + qa G2                 (pair 3+4)
+  TM qb;                  // Qb = q + qb * (first stage's G)
+  TM b6, d6, dt;          // RK4 combine (pair 3+4)
+};
+
+template <class C>
+__device__ __forceinline__ PairCoef<typename C::TM> pair_coef(const Desc *d, long long n) {
+  using TM = typename C::TM;
+  const bool second = C::S == 6;
+  const double dt = d->dt;
+  const double tn = d->t0 + (double)n * dt;
+  const double ta = second ? tn + 0.5 * dt : tn;        // stage 3 | stage 1
+  const double tb = second ? tn + dt : tn + 0.5 * dt;   // stage 4 | stage 2
+  const double ca = exp(-2.0 * ta) * d->inv_h2, cb = exp(-2.0 * tb) * d->inv_h2;
+  PairCoef<TM> k;
+  k.c43a = (TM)(4.0 / 3.0 * ca); k.cm12a = (TM)(-ca / 12.0);
+  k.ccena = C::DIFF ? (TM)d->mu2 : (TM)(d->mu2 - 7.5 * ca);
+  k.c43b = (TM)(4.0 / 3.0 * cb); k.cm12b = (TM)(-cb / 12.0);
+  k.ccenb = C::DIFF ? (TM)d->mu2 : (TM)(d->mu2 - 7.5 * cb);
+  k.nlam = (TM)(-d->lambda);
+  k.m3 = (TM)(-3.0);
+  k.aq = (TM)(second ? 0.5 * dt : 0.0);
+  k.ag = (TM)(second ? 0.25 * dt * dt : 0.0);
+  k.bq = (TM)(second ? dt : 0.5 * dt);
+  k.bg = (TM)(second ? 0.5 * dt * dt : 0.0);
+  k.qa = (TM)(second ? 0.5 * dt : 0.0);
+  k.qb = (TM)(second ? dt : 0.5 * dt);
+  k.b6 = (TM)(dt * dt / 6.0);
+  k.d6 = (TM)(dt / 6.0);
+  k.dt = (TM)dt;
+  return k;
+}
+
+template <class TM>
+__device__ __forceinline__ TM lap_g2(TM c43, TM cm12, TM ccen, TM nlam, TM m3, bool diff, TM P0,
+                                     TM xm2, TM xm1, TM xp1, TM xp2, TM ym2, TM ym1, TM yp1,
+                                     TM yp2, TM zm2, TM zm1, TM zp1, TM zp2, TM Q) {
+  TM s1, s2;
+  if (diff) {
+    s1 = ((xm1 - P0) + (xp1 - P0)) + (((ym1 - P0) + (yp1 - P0)) + ((zm1 - P0) + (zp1 - P0)));
+    s2 = ((xm2 - P0) + (xp2 - P0)) + (((ym2 - P0) + (yp2 - P0)) + ((zm2 - P0) + (zp2 - P0)));
+  } else {
+    s1 = ((xm1 + xp1) + (ym1 + yp1)) + (zm1 + zp1);
+    s2 = ((xm2 + xp2) + (ym2 + yp2)) + (zm2 + zp2);
+  }
+  TM g = fmaT(nlam * (P0 * P0), P0, m3 * Q);
+  g = fmaT(ccen, P0, g);
+  g = fmaT(cm12, s2, g);
+  return fmaT(c43, s1, g);
+}
+
+// Two RK stages per launch.  Pair 1+2: G1 = G(t, p, q) and
+// G2 = G(t + dt/2, p + dt/2 q, q + dt/2 G1) need p and q (with halo) only, and
+// G1 enters G2 at the point.  Pair 3+4: G3 = G(t + dt/2, p + dt/2 q + dt^2/4 G1,
+// q + dt/2 G2) and G4 = G(t + dt, p + dt q + dt^2/2 G2, q + dt G3) need p, q,
+// G1, G2 (with halo) and G3 only at the point, so G3 never leaves the SM; the
+// RK4 combine follows.  Both stage arguments of a pair are formed from the same
+// ring tiles.
+template <class C>
+struct PairConsumer {
+  using TS = typename C::TS;
+  using TG = typename C::TG;
+  using TM = typename C::TM;
+  static constexpr int S = C::S, VEC = C::VEC, VY = C::VY, TX = C::TX;
+  static constexpr int BXS = C::BXS, BXG = C::BXG, HXS = C::HXS, HXG = C::HXG;
+
+  // Both stage arguments at n consecutive positions from (lx, ly).
+  template <int n>
+  static __device__ __forceinline__ void comb2(const unsigned char *base, const PairCoef<TM> &k,
+                                               int lx, int ly, TM (&pa)[n], TM (&pb)[n]) {
+    TM pv[n], qv[n];
+    load_as<TS, TM, n>(reinterpret_cast<const TS *>(base) + (ly + 2) * BXS + lx + HXS, pv);
+    load_as<TS, TM, n>(reinterpret_cast<const TS *>(base + C::HS_BYTES) + (ly + 2) * BXS + lx + HXS, qv);
+    if constexpr (S == 5) {
+#pragma unroll
+      for (int j = 0; j < n; ++j) { pa[j] = pv[j]; pb[j] = fmaT(k.bq, qv[j], pv[j]); }
+    } else {
+      TM g1[n], g2[n];
+      const TG *hg = reinterpret_cast<const TG *>(base + C::OFF_HG) + (ly + 2) * BXG + lx + HXG;
+      load_as<TG, TM, n>(hg, g1);
+      load_as<TG, TM, n>(hg + C::HG_BYTES / (int)sizeof(TG), g2);
+#pragma unroll
+      for (int j = 0; j < n; ++j) {
+        pa[j] = fmaT(k.ag, g1[j], fmaT(k.aq, qv[j], pv[j]));
+        pb[j] = fmaT(k.bg, g2[j], fmaT(k.bq, qv[j], pv[j]));
+      }
+    }
+  }
+
+  // x neighbours of both stage arguments for the lane's VEC points in row ly.
+  static __device__ __forceinline__ void xnb2(const unsigned char *base, const PairCoef<TM> &k,
+                                              int lane, int ly, const TM (&ca)[VEC],
+                                              const TM (&cb)[VEC], TM (&ea)[VEC + 4],
+                                              TM (&eb)[VEC + 4]) {
+    // e[i] = P at x - 2 + i, i = 0 .. VEC + 3
+    if constexpr (VEC >= 2) {
+      TM la0 = shfl_up1(ca[VEC - 2], 1), la1 = shfl_up1(ca[VEC - 1], 1);
+      TM lb0 = shfl_up1(cb[VEC - 2], 1), lb1 = shfl_up1(cb[VEC - 1], 1);
+      TM ra0 = shfl_dn1(ca[0], 1), ra1 = shfl_dn1(ca[1], 1);
+      TM rb0 = shfl_dn1(cb[0], 1), rb1 = shfl_dn1(cb[1], 1);
+      if (lane == 0) {
+        TM ha[2], hb[2];
+        comb2<2>(base, k, -2, ly, ha, hb);
+        la0 = ha[0]; la1 = ha[1]; lb0 = hb[0]; lb1 = hb[1];
+      } else if (lane == 31) {
+        TM ha[2], hb[2];
+        comb2<2>(base, k, TX, ly, ha, hb);
+        ra0 = ha[0]; ra1 = ha[1]; rb0 = hb[0]; rb1 = hb[1];
+      }
+      ea[0] = la0; ea[1] = la1; eb[0] = lb0; eb[1] = lb1;
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) { ea[2 + j] = ca[j]; eb[2 + j] = cb[j]; }
+      ea[VEC + 2] = ra0; ea[VEC + 3] = ra1; eb[VEC + 2] = rb0; eb[VEC + 3] = rb1;
+    } else {
+      TM ha[1] = {ca[0]}, hb[1] = {cb[0]};
+      if (lane < 2) comb2<1>(base, k, lane - 2, ly, ha, hb);
+      else if (lane >= 30) comb2<1>(base, k, TX + lane - 30, ly, ha, hb);
+      const TM a_u2 = shfl_up1(ca[0], 2), a_u1 = shfl_up1(ca[0], 1);
+      const TM a_d2 = shfl_dn1(ca[0], 2), a_d1 = shfl_dn1(ca[0], 1);
+      const TM b_u2 = shfl_up1(cb[0], 2), b_u1 = shfl_up1(cb[0], 1);
+      const TM b_d2 = shfl_dn1(cb[0], 2), b_d1 = shfl_dn1(cb[0], 1);
+      const TM a_h1 = shfl_idx(ha[0], 1), a_h30 = shfl_idx(ha[0], 30);
+      const TM b_h1 = shfl_idx(hb[0], 1), b_h30 = shfl_idx(hb[0], 30);
+      ea[0] = lane < 2 ? ha[0] : a_u2;
+      ea[1] = lane == 0 ? a_h1 : a_u1;
+      ea[2] = ca[0];
+      ea[3] = lane == 31 ? a_h30 : a_d1;
+      ea[4] = lane >= 30 ? ha[0] : a_d2;
+      eb[0] = lane < 2 ? hb[0] : b_u2;
+      eb[1] = lane == 0 ? b_h1 : b_u1;
+      eb[2] = cb[0];
+      eb[3] = lane == 31 ? b_h30 : b_d1;
+      eb[4] = lane >= 30 ? hb[0] : b_d2;
+    }
+  }
+
+  static __device__ __forceinline__ void run(const StageParams &prm, uint64_t *full,
+                                             uint64_t *empty, const unsigned char *ring,
+                                             volatile int *abort_flag, int warp, int lane) {
+    constexpr int RING = C::RING;
+    const int nitems = *prm.nitems;
+    const int lx0 = lane * VEC, ly0 = warp * VY;
+    int slot = 0;
+    uint32_t phase = 0;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+      const WorkItem w = prm.items[it];
+      Desc *d = prm.descs + w.x;
+      if (!item_active<S>(d, prm.k, warp == 0 && lane == 0)) continue;
+      const long long n = d->n_base + prm.k;
+      PairCoef<TM> k;
+      {
+        PairCoef<TM> c0;
+        if (lane == 0) c0 = pair_coef<C>(d, n);
+        const TM *src = reinterpret_cast<const TM *>(&c0);
+        TM *dst = reinterpret_cast<TM *>(&k);
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(PairCoef<TM>) / sizeof(TM)); ++i)
+          dst[i] = shfl_idx(src[i], 0);
+      }
+      const int N = d->N;
+      const bool periodic = d->bc == 1;
+      const int set = (int)(n & 1);
+      const int so = set ^ 1;
+      const int x0 = (w.y & 0xffff) * TX, y0 = (w.y >> 16) * C::TY;
+      const int z0 = w.z, nplanes = w.w + 4;
+      const bool ragged = x0 + TX > N;
+      const int x = x0 + lx0;
+      const bool lane_edge = periodic && (x < 2 || x + VEC > N - 2);
+      const int64_t pitch_s = d->pitch_s, plane_s = d->plane_s;
+      const int64_t pitch_g = d->pitch_g, plane_g = d->plane_g;
+      const int64_t row_s = (int64_t)(y0 + ly0 + 2) * pitch_s + HXS + x;
+      const int64_t row_g = (int64_t)(y0 + ly0 + 2) * pitch_g + HXG + x;
+      const bool xok = x < N;
+      TG *outG1 = nullptr, *outG2 = nullptr;
+      TS *outP = nullptr, *outQ = nullptr, *outPL = nullptr, *outQL = nullptr;
+      if constexpr (S == 5) {
+        outG1 = reinterpret_cast<TG *>(d->f[F_G1]);
+        outG2 = reinterpret_cast<TG *>(d->f[F_G2]);
+      } else {
+        outP = reinterpret_cast<TS *>(d->f[F_P0 + so]);
+        outQ = reinterpret_cast<TS *>(d->f[F_Q0 + so]);
+        if constexpr (C::KAHAN) {
+          outPL = reinterpret_cast<TS *>(d->f[F_PLO0 + so]);
+          outQL = reinterpret_cast<TS *>(d->f[F_QLO0 + so]);
+        }
+      }
+      bool rok[VY];
+#pragma unroll
+      for (int r = 0; r < VY; ++r) rok[r] = xok && (y0 + ly0 + r < N);
+
+      TM wa[5][VY][VEC], wb[5][VY][VEC];
+#pragma unroll
+      for (int a = 0; a < 5; ++a)
+#pragma unroll
+        for (int r = 0; r < VY; ++r)
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) { wa[a][r][j] = (TM)0; wb[a][r][j] = (TM)0; }
+      TM run_max = (TM)0;
+
+      for (int m = 0; m < nplanes; ++m) {
+        if (!mbar_wait_bounded(&full[slot], phase)) {
+          *abort_flag = 1;
+          atomicOr(prm.err, (unsigned)DEV_ERR_TIMEOUT);
+          return;
+        }
+        if (*abort_flag) return;
+        const unsigned char *base = ring + slot * C::SLOT_BYTES;
+#pragma unroll
+        for (int r = 0; r < VY; ++r) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) { wa[a][r][j] = wa[a + 1][r][j]; wb[a][r][j] = wb[a + 1][r][j]; }
+          comb2<VEC>(base, k, lx0, ly0 + r, wa[4][r], wb[4][r]);
+        }
+        const int s2 = slot >= 2 ? slot - 2 : slot + RING - 2;
+        if (m >= 4) {
+          const int z = z0 + m - 4;
+          const unsigned char *b2 = ring + s2 * C::SLOT_BYTES;
+          TM Ra[VY + 4][VEC], Rb[VY + 4][VEC];
+          comb2<VEC>(b2, k, lx0, ly0 - 2, Ra[0], Rb[0]);
+          comb2<VEC>(b2, k, lx0, ly0 - 1, Ra[1], Rb[1]);
+          comb2<VEC>(b2, k, lx0, ly0 + VY, Ra[VY + 2], Rb[VY + 2]);
+          comb2<VEC>(b2, k, lx0, ly0 + VY + 1, Ra[VY + 3], Rb[VY + 3]);
+#pragma unroll
+          for (int r = 0; r < VY; ++r)
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) { Ra[r + 2][j] = wa[2][r][j]; Rb[r + 2][j] = wb[2][r][j]; }
+#pragma unroll
+          for (int r = 0; r < VY; ++r) {
+            const int ly = ly0 + r;
+            const int y = y0 + ly;
+            TM ea[VEC + 4], eb[VEC + 4];
+            xnb2(b2, k, lane, ly, wa[2][r], wb[2][r], ea, eb);
+            const int hoff = (ly + 2) * BXS + lx0 + HXS;
+            TM qS[VEC];
+            load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(b2 + C::HS_BYTES) + hoff, qS);
+            TM Ga[VEC], Gb[VEC], g1[VEC], g2[VEC];
+            if constexpr (S == 6) {
+              const TG *hg = reinterpret_cast<const TG *>(b2 + C::OFF_HG) + (ly + 2) * BXG + lx0 + HXG;
+              load_as<TG, TM, VEC>(hg, g1);
+              load_as<TG, TM, VEC>(hg + C::HG_BYTES / (int)sizeof(TG), g2);
+            }
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) {
+              const TM Qa = (S == 6) ? fmaT(k.qa, g2[j], qS[j]) : qS[j];
+              Ga[j] = lap_g2(k.c43a, k.cm12a, k.ccena, k.nlam, k.m3, C::DIFF, wa[2][r][j], ea[j],
+                             ea[j + 1], ea[j + 3], ea[j + 4], Ra[r][j], Ra[r + 1][j], Ra[r + 3][j],
+                             Ra[r + 4][j], wa[0][r][j], wa[1][r][j], wa[3][r][j], wa[4][r][j], Qa);
+              const TM Qb = fmaT(k.qb, Ga[j], qS[j]);
+              Gb[j] = lap_g2(k.c43b, k.cm12b, k.ccenb, k.nlam, k.m3, C::DIFF, wb[2][r][j], eb[j],
+                             eb[j + 1], eb[j + 3], eb[j + 4], Rb[r][j], Rb[r + 1][j], Rb[r + 3][j],
+                             Rb[r + 4][j], wb[0][r][j], wb[1][r][j], wb[3][r][j], wb[4][r][j], Qb);
+            }
+            if (!rok[r]) continue;
+            const bool edge = lane_edge || (periodic && (y < 2 || y >= N - 2));
+            if constexpr (S == 5) {
+              const int64_t off = (int64_t)z * plane_g + row_g + r * pitch_g - x;
+              store_point<TG, TM, VEC>(outG1 + off, pitch_g, N, ragged, edge, x, y, Ga);
+              store_point<TG, TM, VEC>(outG2 + off, pitch_g, N, ragged, edge, x, y, Gb);
+            } else {
+              // RK4 combine (Sec. 2.1) with G3 = Ga, G4 = Gb
+              TM pS[VEC], lp[VEC], lq[VEC];
+              load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(b2) + hoff, pS);
+              if constexpr (C::KAHAN) {
+                const TS *is = reinterpret_cast<const TS *>(b2 + C::OFF_IS) + ly * TX + lx0;
+                load_as<TS, TM, VEC>(is, lp);
+                load_as<TS, TM, VEC>(is + C::IS_BYTES / (int)sizeof(TS), lq);
+              }
+              TM pn[VEC], qn[VEC], pl[VEC], ql[VEC];
+#pragma unroll
+              for (int j = 0; j < VEC; ++j) {
+                const TM dp = fmaT(k.b6, (g1[j] + g2[j]) + Ga[j], k.dt * qS[j]);
+                const TM dq = k.d6 * ((g1[j] + Gb[j]) + (TM)2 * (g2[j] + Ga[j]));
+                if constexpr (C::KAHAN) {
+                  two_sum(pS[j], dp + lp[j], pn[j], pl[j]);
+                  two_sum(qS[j], dq + lq[j], qn[j], ql[j]);
+                } else {
+                  pn[j] = pS[j] + dp;
+                  qn[j] = qS[j] + dq;
+                }
+                if (x + j < N) {
+                  const TM av = pn[j] < (TM)0 ? -pn[j] : pn[j];
+                  run_max = (av <= run_max) ? run_max : ((av == av) ? av : (TM)INFINITY);
+                }
+              }
+              const int64_t off = (int64_t)z * plane_s + row_s + r * pitch_s - x;
+              store_point<TS, TM, VEC>(outP + off, pitch_s, N, ragged, edge, x, y, pn);
+              store_point<TS, TM, VEC>(outQ + off, pitch_s, N, ragged, edge, x, y, qn);
+              if constexpr (C::KAHAN) {
+                store_point<TS, TM, VEC>(outPL + off, pitch_s, N, ragged, edge, x, y, pl);
+                store_point<TS, TM, VEC>(outQL + off, pitch_s, N, ragged, edge, x, y, ql);
+              }
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          if (m < 2 || m >= nplanes - 2) mbar_arrive(&empty[slot]);
+          if (m >= 4) mbar_arrive(&empty[s2]);
+        }
+        if (++slot == RING) { slot = 0; phase ^= 1u; }
+      }
+      if constexpr (S == 6) {
+        double v = (double)run_max;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) atomicMax(d->maxabs + prm.k, (unsigned long long)__double_as_longlong(v));
+      }
+    }
+  }
+};
+
 template <class C>
 __global__ void __launch_bounds__(C::THREADS, C::MINB)
     stage_kernel(const StageParams prm) {
@@ -679,6 +1047,8 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
   __syncthreads();
   if (warp == C::NW) {
     if (lane == 0) produce<C>(prm, full, empty, ring, abort_flag);
+  } else if constexpr (C::PAIR) {
+    PairConsumer<C>::run(prm, full, empty, ring, abort_flag, warp, lane);
   } else {
     Consumer<C>::run(prm, full, empty, ring, abort_flag, warp, lane);
   }

@@ -16,6 +16,8 @@ void add(VariantTable &t) {
   k[1] = info<StageCfg<PR, V, VY, NW, B, MB, 2>>();
   k[2] = info<StageCfg<PR, V, VY, NW, B, MB, 3>>();
   k[3] = info<StageCfg<PR, V, VY, NW, B, MB, 4>>();
+  k[4] = info<StageCfg<PR, V, VY, NW, B, MB, 5>>();
+  k[5] = info<StageCfg<PR, V, VY, NW, B, MB, 6>>();
 }
 }  // namespace
 
@@ -24,10 +26,10 @@ const VariantTable &variants_bf16() {
     using PR = PrecBF16;
     VariantTable t{};
     // <precision, x points per lane, rows per warp, consumer warps, smem budget, min blocks/SM>
+    add<PR, 4, 1, 8, 110 * 1024, 2>(t);  // 128 x 8 tile, 9 warps
+    add<PR, 4, 1, 8, 220 * 1024, 1>(t);  // 128 x 8 tile, 9 warps, deep ring
+    add<PR, 4, 1, 4, 110 * 1024, 2>(t);  // 128 x 4 tile, 5 warps
     add<PR, 2, 1, 8, 110 * 1024, 2>(t);  // 64 x 8 tile, 9 warps
-    add<PR, 2, 2, 8, 220 * 1024, 1>(t);  // 64 x 16 tile, 9 warps
-    add<PR, 2, 2, 4, 110 * 1024, 2>(t);  // 64 x 8 tile, 5 warps
-    add<PR, 1, 2, 8, 110 * 1024, 2>(t);  // 32 x 16 tile, 9 warps
     return t;
   }();
   return table;

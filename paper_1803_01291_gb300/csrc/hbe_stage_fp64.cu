@@ -16,6 +16,8 @@ void add(VariantTable &t) {
   k[1] = info<StageCfg<PR, V, VY, NW, B, MB, 2>>();
   k[2] = info<StageCfg<PR, V, VY, NW, B, MB, 3>>();
   k[3] = info<StageCfg<PR, V, VY, NW, B, MB, 4>>();
+  k[4] = info<StageCfg<PR, V, VY, NW, B, MB, 5>>();
+  k[5] = info<StageCfg<PR, V, VY, NW, B, MB, 6>>();
 }
 }  // namespace
 

@@ -18,7 +18,8 @@ constexpr int kMaxVariants = 4;
 
 struct VariantTable {
   int count;
-  KernelInfo k[kMaxVariants][4];  // [variant][stage-1]
+  // [variant][0..3] one RK stage per launch; [4] stages 1+2; [5] stages 3+4 + combine
+  KernelInfo k[kMaxVariants][6];
 };
 
 const VariantTable &variants_fp64();

@@ -179,7 +179,9 @@ class Server:
                 steps, _ = s.progress()
                 d = s.diag()  # the result: max|phi|, finiteness, bubble count
                 phi = s.read(psi=False)[0] if self.keep_fields else None
-                stats.results.append(Result(req.rid, req.arrival, admitted, clock() - t0, steps,
+                # closed-loop runs treat every request as arrived at the start
+                arrived = req.arrival if realtime else 0.0
+                stats.results.append(Result(req.rid, arrived, admitted, clock() - t0, steps,
                                             st, d["max_abs_phi"], phi))
                 s.close()
                 self.in_use -= nb
