@@ -42,14 +42,18 @@ PREC_BYTES = {"fp64": (8, 8, False), "fp32": (4, 4, True), "bf16": (4, 2, True),
               "fp32_plain": (4, 4, False)}
 
 
-def stage_bytes(prec: str):
+def stage_bytes(prec: str, schedule: int = 1):
+    """Algorithmic bytes per grid point of each launch of one RK4 step."""
     s, g, comp = PREC_BYTES[prec]
+    lo = 4 * s if comp else 0      # lo parts of p and q, in and out
+    if schedule == 1:
+        a = 2 * s + 2 * g          # p, q -> G1, G2
+        b = 2 * s + 2 * g + 2 * s + lo  # p, q, G1, G2 -> p', q'
+        return [a, b]
     b1 = 2 * s + g                 # p, q -> G1
     b2 = 2 * s + 2 * g             # p, q, G1 -> G2
     b3 = 2 * s + 3 * g             # p, q, G1, G2 -> G3
-    b4 = 2 * s + 3 * g + 2 * s     # p, q, G1, G2, G3 -> p', q'
-    if comp:
-        b4 += 4 * s                # lo parts of p and q, in and out
+    b4 = 2 * s + 3 * g + 2 * s + lo  # p, q, G1, G2, G3 -> p', q'
     return [b1, b2, b3, b4]
 
 
@@ -75,10 +79,21 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(prec: str, N: int):
-    """dram bytes per launch of the stage-4 kernel from the committed ncu summary,
+def tuned(hbe, N: int, bc: int, prec: int):
+    """(variant, zchunk, schedule) from the autotuner cache if present, else
+    the library's defaults."""
+    from paper_1803_01291_gb300 import autotune
+    try:
+        return autotune.best(N, bc, prec)
+    except Exception:
+        return (0, 0, 1)
+
+
+def recorded_traffic(prec: str, N: int, schedule: int = 1):
+    """dram bytes per launch of the dominant kernel from the committed ncu summary,
     if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", f"stage4_{prec}_traffic.txt")
+    kind = "pair34" if schedule == 1 else "stage4"
+    path = os.path.join(ROOT, "profiles", f"{kind}_{prec}_traffic.txt")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -187,10 +202,14 @@ def workload(N: int):
     return prob
 
 
-def time_path(hbe, torch, prob, prec_id, steps, warmup, profile_warm=True):
-    """Warm up, then time `steps` RK4 steps with the four stage kernels each
-    bracketed by CUDA events on the solver's stream.  Returns (seconds, per-stage ms)."""
+def time_path(hbe, torch, prob, prec_id, steps, warmup, schedule=1, tuning=None):
+    """Warm up, then time `steps` RK4 steps with the step's kernels each
+    bracketed by CUDA events on the solver's stream.  Returns (seconds,
+    per-launch ms, launches in the timed region)."""
     s = hbe.Solver(prob.N, prob.L, prob.mu, prob.lam, prob.bc, prec_id)
+    s.set_schedule(schedule)
+    if tuning is not None:
+        s.set_tuning(tuning[0], tuning[1])
     phi0 = torch.from_numpy(prob.phi0).cuda()
     phi1 = torch.from_numpy(prob.phi1).cuda()
     s.set_initial(phi0, phi1)
@@ -206,8 +225,8 @@ def time_path(hbe, torch, prob, prec_id, steps, warmup, profile_warm=True):
     e1.record(stream)
     torch.cuda.synchronize()
     secs = e0.elapsed_time(e1) / 1e3
-    # 4 stage kernels per step (counted by the library) + the per-step
-    # bookkeeping kernel + one run-setup kernel
+    # the step's kernels (counted by the library) + the per-step bookkeeping
+    # kernel + one run-setup kernel
     launches = s.launches - l0 + steps + 1
     s.close()
     return secs, stage_ms, launches
@@ -356,6 +375,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--schedule", type=int, default=None, choices=[0, 1],
+                    help="0: one kernel per RK stage, 1: two fused stage pairs per step "
+                         "(default: the autotuner's choice, else 1)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -377,27 +399,37 @@ def main():
     hbm_peak, peak_kind = measured_peaks()
 
     # headline: FP32 with compensated state; each rank solves its own replica
+    tuning = tuned(hbe, N, prob.bc, hbe.FP32)
+    if args.schedule is None:
+        args.schedule = tuning[2]
     barrier(world, torch)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        secs, stage_ms, launches = time_path(hbe, torch, prob, hbe.FP32, args.steps, args.warmup)
+        secs, stage_ms, launches = time_path(hbe, torch, prob, hbe.FP32, args.steps, args.warmup,
+                                             args.schedule, tuning)
     secs = max_over_ranks(secs, world, torch, device)
     barrier(world, torch)
     value = aggregate(float(N) ** 3 * args.steps, secs, world)
 
-    sb = stage_bytes("fp32")
-    stage_gbs = [sb[i] * N ** 3 / (stage_ms[i] / 1e3) / 1e9 for i in range(4)]
-    traffic = recorded_traffic("fp32", N)
-    roofline = {"bound": "hbm", "kernel": "stage_kernel<FP32, stage 4> (RK4 combine)",
-                "achieved": stage_gbs[3], "peak": hbm_peak, "unit": "GB/s",
-                "frac": stage_gbs[3] / hbm_peak, "peak_kind": peak_kind,
+    sb = stage_bytes("fp32", args.schedule)
+    nl = len(sb)
+    stage_gbs = [sb[i] * N ** 3 / (stage_ms[i] / 1e3) / 1e9 for i in range(nl)]
+    dom = max(range(nl), key=lambda i: stage_ms[i])   # the dominant kernel
+    names = (["stages 1+2", "stages 3+4 + RK4 combine"] if args.schedule == 1 else
+             ["stage 1", "stage 2", "stage 3", "stage 4 + RK4 combine"])
+    traffic = recorded_traffic("fp32", N, args.schedule)
+    step_gbs = sum(sb) * N ** 3 * args.steps / secs / 1e9
+    roofline = {"bound": "hbm", "kernel": f"stage_kernel<FP32> {names[dom]}",
+                "achieved": stage_gbs[dom], "peak": hbm_peak, "unit": "GB/s",
+                "frac": stage_gbs[dom] / hbm_peak, "peak_kind": peak_kind,
                 "traffic": traffic,
-                "algorithmic_bytes_per_launch": sb[3] * N ** 3,
-                "step": {"bytes_per_point": sum(sb), "achieved_gbs": sum(sb) * N ** 3 * args.steps / secs / 1e9,
-                         "frac": sum(sb) * N ** 3 * args.steps / secs / 1e9 / hbm_peak},
-                "stages": [{"stage": i + 1, "ms": stage_ms[i], "bytes_per_point": sb[i],
-                            "gbs": stage_gbs[i], "frac": stage_gbs[i] / hbm_peak}
-                           for i in range(4)]}
+                "algorithmic_bytes_per_launch": sb[dom] * N ** 3,
+                "step": {"bytes_per_point": sum(sb), "achieved_gbs": step_gbs,
+                         "frac": step_gbs / hbm_peak},
+                "launches": [{"kernel": names[i], "ms": stage_ms[i], "bytes_per_point": sb[i],
+                              "gbs": stage_gbs[i], "frac": stage_gbs[i] / hbm_peak}
+                             for i in range(nl)],
+                "schedule": args.schedule, "tuning": {"variant": tuning[0], "zchunk": tuning[1]}}
 
     line = {
         "metric": METRIC,
@@ -416,8 +448,9 @@ def main():
         for name, pid, steps in (("fp64", hbe.FP64, max(10, args.steps // 10)),
                                  ("bf16", hbe.BF16, args.steps),
                                  ("fp32_plain", hbe.FP32_PLAIN, args.steps)):
-            s2, ms2, _ = time_path(hbe, torch, prob, pid, steps, 3)
-            sbp = stage_bytes(name)
+            s2, ms2, _ = time_path(hbe, torch, prob, pid, steps, 3, args.schedule,
+                                   tuned(hbe, N, prob.bc, pid))
+            sbp = stage_bytes(name, args.schedule)
             v = float(N) ** 3 * steps / s2 / 1e9
             entry = {"value": v, "unit": "Gpoint-steps/s", "steps": steps,
                      "ms_per_step": s2 / steps * 1e3, "stage_ms": ms2,

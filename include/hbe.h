@@ -117,6 +117,14 @@ hbe_status hbe_set_stream(hbe_ctx *ctx, void *stream);
  * z-chunk length (planes per block work item; 0 = whole column). */
 hbe_status hbe_set_tuning(hbe_ctx *ctx, int variant, int zchunk);
 hbe_status hbe_variant_info(int prec, int variant, hbe_variant_t *out);
+
+/* Kernel schedule of one RK4 step (both compute the same step of Sec. 2.1):
+ *   0: four launches, one per RK stage (stage s writes G_s; stage 4 applies
+ *      the RK4 combine);
+ *   1 (default): two launches, stages 1+2 together (G1, G2 from p, q) and
+ *      stages 3+4 together with the combine (G3 stays on chip), which moves
+ *      14 instead of 19 field passes per step. */
+hbe_status hbe_set_schedule(hbe_ctx *ctx, int schedule);
 int hbe_variant_count(int prec);
 
 /* Initial data (Eq. HBEinit) at time t0: host arrays of N^3 doubles, copied. */
@@ -156,10 +164,12 @@ hbe_status hbe_sync(hbe_ctx *ctx);
 hbe_status hbe_read(hbe_ctx *ctx, double *phi, double *psi, double *t);
 /* Same to device arrays on the context's stream (not synchronised). */
 hbe_status hbe_read_device(hbe_ctx *ctx, double *d_phi, double *d_psi);
-/* Profiling aid: nsteps (1..4096) RK4 steps with the four stage kernels
- * launched one at a time (no graph) and each bracketed by CUDA events on the
- * context's stream; ms_per_stage[s] receives the mean duration of stage s+1
- * (4 floats, caller-owned).  The state advances as with hbe_step.  Blocks. */
+/* Profiling aid: nsteps (1..4096) RK4 steps with the step's kernels launched
+ * one at a time (no graph), each bracketed by CUDA events on the context's
+ * stream; ms_per_stage[i] receives the mean duration of the i-th launch of a
+ * step (4 floats, caller-owned; schedule 1 fills [0] = stages 1+2 and
+ * [1] = stages 3+4 and sets [2], [3] to 0).  The state advances as with
+ * hbe_step.  Blocks. */
 hbe_status hbe_profile_stages(hbe_ctx *ctx, int64_t nsteps, double dt, float *ms_per_stage);
 
 /* Steps taken and current time. */
@@ -170,6 +180,29 @@ hbe_status hbe_progress(hbe_ctx *ctx, int64_t *steps, double *t);
  * either may be NULL) and the component counts.  Blocks. */
 hbe_status hbe_diag(hbe_ctx *ctx, double eps, hbe_diag_t *out, uint32_t *pos_mask,
                     uint32_t *neg_mask);
+
+/* The analysis quantities of Sec. 3 on the current state (double precision):
+ *   integral_phi      = h^3 sum phi: the integral of phi over the box, whose
+ *                       blow-up marks the blow-up of Example 2 (Sec. 3);
+ *   integral_phi3     = h^3 sum phi^3: the second bubble condition of the
+ *                       corollary quoted in Example 3 asks it to stay >= 0;
+ *   laplacian_monitor = e^{-2t} max |FD4 Laplacian of phi|: the quantity
+ *                       P(t) of Example 4 (physical units), whose decay shows
+ *                       the approach to the Duffing limit;
+ *   support_points    = nodes with |phi| + |psi| > eps;
+ *   condition1_violations = support nodes where (3/2 + sqrt(9/4 + mu^2)) phi +
+ *                       psi >= 0, i.e. where the first bubble condition of that
+ *                       corollary (read at the current time) fails.
+ * The sums are added in a fixed order (bitwise reproducible).  Blocks. */
+typedef struct {
+  double t;
+  double integral_phi;
+  double integral_phi3;
+  double laplacian_monitor;
+  int64_t support_points;
+  int64_t condition1_violations;
+} hbe_analysis_t;
+hbe_status hbe_analysis(hbe_ctx *ctx, double eps, hbe_analysis_t *out);
 
 /* Raw state (both fields in storage precision, step count, t0, dt) to/from
  * a file; a load into a context of the same N, bc and precision continues

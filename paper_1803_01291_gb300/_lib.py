@@ -18,9 +18,9 @@ PREC_NAMES = {FP64: "fp64", FP32: "fp32", BF16: "bf16", FP32_PLAIN: "fp32_plain"
 # every entry point declared in include/hbe.h
 EXPORTS = (
     "hbe_workspace_bytes", "hbe_create", "hbe_create_in", "hbe_destroy", "hbe_set_stream",
-    "hbe_set_tuning", "hbe_variant_info", "hbe_variant_count", "hbe_set_initial",
+    "hbe_set_tuning", "hbe_set_schedule", "hbe_variant_info", "hbe_variant_count", "hbe_set_initial",
     "hbe_set_initial_device", "hbe_set_initial_bumps", "hbe_set_stop", "hbe_step", "hbe_step_async", "hbe_sync",
-    "hbe_read", "hbe_read_device", "hbe_profile_stages", "hbe_progress", "hbe_diag", "hbe_save", "hbe_load",
+    "hbe_read", "hbe_read_device", "hbe_profile_stages", "hbe_progress", "hbe_analysis", "hbe_diag", "hbe_save", "hbe_load",
     "hbe_last_error", "hbe_status_string", "hbe_launch_count", "hbe_batch_create",
     "hbe_batch_destroy", "hbe_batch_add", "hbe_batch_remove", "hbe_batch_run",
     "hbe_batch_size", "hbe_batch_last_error", "hbe_batch_launch_count", "hbe_step_fp64_noalloc",
@@ -32,6 +32,12 @@ class HbeDiag(ctypes.Structure):
                 ("max_abs_phi", ctypes.c_double), ("finite", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("n_pos", ctypes.c_int64),
                 ("n_neg", ctypes.c_int64), ("bubble_count", ctypes.c_int64)]
+
+
+class HbeAnalysis(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("integral_phi", ctypes.c_double),
+                ("integral_phi3", ctypes.c_double), ("laplacian_monitor", ctypes.c_double),
+                ("support_points", ctypes.c_int64), ("condition1_violations", ctypes.c_int64)]
 
 
 class HbeVariant(ctypes.Structure):
@@ -76,6 +82,7 @@ def load() -> ctypes.CDLL:
             "hbe_destroy": (None, [P]),
             "hbe_set_stream": (I, [P, P]),
             "hbe_set_tuning": (I, [P, I, I]),
+            "hbe_set_schedule": (I, [P, I]),
             "hbe_variant_info": (I, [I, I, ctypes.POINTER(HbeVariant)]),
             "hbe_variant_count": (I, [I]),
             "hbe_set_initial": (I, [P, dp, dp, D]),
@@ -90,6 +97,7 @@ def load() -> ctypes.CDLL:
             "hbe_progress": (I, [P, ctypes.POINTER(I64), dp]),
             "hbe_profile_stages": (I, [P, I64, D, ctypes.POINTER(ctypes.c_float)]),
             "hbe_diag": (I, [P, D, ctypes.POINTER(HbeDiag), P, P]),
+            "hbe_analysis": (I, [P, D, ctypes.POINTER(HbeAnalysis)]),
             "hbe_save": (I, [P, ctypes.c_char_p]),
             "hbe_load": (I, [P, ctypes.c_char_p]),
             "hbe_last_error": (ctypes.c_char_p, [P]),

@@ -1,9 +1,10 @@
-"""Tile-shape / z-chunk autotuner for the stage kernels.
+"""Schedule / tile-shape / z-chunk autotuner for the stage kernels.
 
-For a problem size N, boundary kind and precision, every compiled tile
-variant is run with a few z-chunk lengths on synthetic data of that size;
-the fastest (variant, zchunk) is kept in a JSON cache keyed by GPU name, N,
-boundary and precision.  The cache path is $HBE_AUTOTUNE_CACHE, else
+For a problem size N, boundary kind and precision, both kernel schedules
+(four one-stage launches per step, or two fused stage pairs) are run with
+every compiled tile variant and a few z-chunk lengths on synthetic data of
+that size; the fastest (variant, zchunk, schedule) is kept in a JSON cache
+keyed by GPU name, N, boundary and precision.  The cache path is $HBE_AUTOTUNE_CACHE, else
 ~/.cache/hbe_autotune.json.
 """
 from __future__ import annotations
@@ -65,8 +66,8 @@ def zchunk_candidates(N: int) -> Iterable[int]:
 
 
 def measure(N: int, bc: int, prec: int, variant: int, zchunk: int, steps: int = 10,
-            warmup: int = 3, seed: int = 0) -> float:
-    """Seconds per RK4 step of one (variant, zchunk) on smooth random data."""
+            warmup: int = 3, seed: int = 0, schedule: int = 1) -> float:
+    """Seconds per RK4 step of one (variant, zchunk, schedule) on smooth random data."""
     import torch
     rng = np.random.default_rng(seed)
     # smooth data: low Fourier modes only (no stop rule, no special values)
@@ -78,6 +79,7 @@ def measure(N: int, bc: int, prec: int, variant: int, zchunk: int, steps: int = 
     h = L / N if bc == _lib.PERIODIC else L / (N + 1)
     with Solver(N, L, 1.0, 1.0, bc, prec) as s:
         s.set_tuning(variant, zchunk)
+        s.set_schedule(schedule)
         s.set_initial(torch.from_numpy(phi0).cuda(), torch.zeros((N, N, N), dtype=torch.float64,
                                                                   device="cuda"))
         s.step(warmup, h / 4)
@@ -94,19 +96,20 @@ def measure(N: int, bc: int, prec: int, variant: int, zchunk: int, steps: int = 
 
 def tune(N: int, bc: int, prec: int, steps: int = 10, save: bool = True,
          verbose: bool = False) -> dict:
-    """Sweep every variant x z-chunk; return and cache the fastest."""
+    """Sweep every schedule x variant x z-chunk; return and cache the fastest."""
     results = []
-    for v in range(len(variants(prec))):
-        for zc in zchunk_candidates(N):
-            t = measure(N, bc, prec, v, zc, steps)
-            results.append((t, v, zc))
-            if verbose:
-                print(f"N={N} bc={bc} prec={_lib.PREC_NAMES[prec]} variant={v} zchunk={zc}: "
-                      f"{t * 1e3:.3f} ms/step")
-    t, v, zc = min(results)
-    entry = {"variant": v, "zchunk": zc, "ms_per_step": t * 1e3,
+    for sch in (1, 0):
+        for v in range(len(variants(prec))):
+            for zc in zchunk_candidates(N):
+                t = measure(N, bc, prec, v, zc, steps, schedule=sch)
+                results.append((t, v, zc, sch))
+                if verbose:
+                    print(f"N={N} bc={bc} prec={_lib.PREC_NAMES[prec]} schedule={sch} "
+                          f"variant={v} zchunk={zc}: {t * 1e3:.3f} ms/step")
+    t, v, zc, sch = min(results)
+    entry = {"variant": v, "zchunk": zc, "schedule": sch, "ms_per_step": t * 1e3,
              "gpoint_steps_per_s": N ** 3 / t / 1e9,
-             "sweep": [[vv, zz, tt * 1e3] for tt, vv, zz in results]}
+             "sweep": [[vv, zz, ss, tt * 1e3] for tt, vv, zz, ss in results]}
     if save:
         with _lock:
             cache = load_cache()
@@ -115,22 +118,23 @@ def tune(N: int, bc: int, prec: int, steps: int = 10, save: bool = True,
     return entry
 
 
-def best(N: int, bc: int, prec: int, tune_missing: bool = False) -> Tuple[int, int]:
-    """(variant, zchunk) for this size from the cache; (0, 0) = the library's
-    default when nothing is cached (or tune now if tune_missing)."""
+def best(N: int, bc: int, prec: int, tune_missing: bool = False) -> Tuple[int, int, int]:
+    """(variant, zchunk, schedule) for this size from the cache; (0, 0, 1) =
+    the library's default when nothing is cached (or tune now if tune_missing)."""
     cache = load_cache()
     e = cache.get(_key(N, bc, prec))
     if e is None and tune_missing:
         e = tune(N, bc, prec)
     if e is None:
-        return 0, 0
-    return int(e["variant"]), int(e["zchunk"])
+        return 0, 0, 1
+    return int(e["variant"]), int(e["zchunk"]), int(e.get("schedule", 1))
 
 
-def apply(solver: Solver, tune_missing: bool = False) -> Tuple[int, int]:
-    v, zc = best(solver.N, solver.bc, solver.prec, tune_missing)
+def apply(solver: Solver, tune_missing: bool = False) -> Tuple[int, int, int]:
+    v, zc, sch = best(solver.N, solver.bc, solver.prec, tune_missing)
     solver.set_tuning(v, zc)
-    return v, zc
+    solver.set_schedule(sch)
+    return v, zc, sch
 
 
 if __name__ == "__main__":
@@ -144,5 +148,6 @@ if __name__ == "__main__":
     prec = {v: k for k, v in _lib.PREC_NAMES.items()}[args.prec]
     for n in args.N:
         e = tune(n, args.bc, prec, args.steps, verbose=True)
-        print(json.dumps({"N": n, "best": {k: e[k] for k in ("variant", "zchunk", "ms_per_step",
+        print(json.dumps({"N": n, "best": {k: e[k] for k in ("variant", "zchunk", "schedule",
+                                                               "ms_per_step",
                                                                "gpoint_steps_per_s")}}))

@@ -70,7 +70,8 @@ struct hbe_ctx {
   int *d_nitems = nullptr;
   int *d_one = nullptr;
   int nitems = 0, items_cap = 0;
-  int grid[4] = {0, 0, 0, 0};
+  int grid[6] = {0, 0, 0, 0, 0, 0};
+  int schedule = 1;  // 0: four one-stage kernels per step; 1: two fused stage pairs
   unsigned *d_err = nullptr;
   int K = 8;
   cudaGraphExec_t gexec = nullptr;
@@ -79,6 +80,7 @@ struct hbe_ctx {
   uint32_t *d_masks = nullptr;
   int *d_labels = nullptr;
   unsigned long long *d_counts = nullptr;
+  double *d_part = nullptr;  // analysis partials (5 x blocks) + result (5)
   bool has_state = false;
   bool pending = false;        // device work enqueued since the last sync
   bool desc_stale = false;     // device descriptor older than the host mirror
@@ -98,7 +100,7 @@ struct hbe_batch {
     WorkItem *d_items = nullptr;
     int *d_n = nullptr;
     int cap = 0;
-    int grid[4] = {0, 0, 0, 0};
+    int grid[6] = {0, 0, 0, 0, 0, 0};
   } lists[kMaxVariants];
   int nvariants = 0;
   unsigned *d_err = nullptr;
@@ -242,7 +244,7 @@ hbe_status apply_tuning(hbe_ctx *ctx, int variant, int zchunk) {
   CK(cudaMemcpy(ctx->d_tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice));
   // persistent grid per stage and the work list
   int resident = 1 << 30;
-  for (int s = 0; s < 4; ++s) {
+  for (int s = 0; s < 6; ++s) {
     if ((st = persistent_grid(ctx->err, ks[s], ctx->sms, &ctx->grid[s]))) return st;
     resident = std::min(resident, ctx->grid[s]);
   }
@@ -260,7 +262,7 @@ hbe_status apply_tuning(hbe_ctx *ctx, int variant, int zchunk) {
   CK(cudaMemcpy(ctx->d_items, items.data(), items.size() * sizeof(WorkItem),
                 cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_nitems, &ctx->nitems, sizeof(int), cudaMemcpyHostToDevice));
-  for (int s = 0; s < 4; ++s) ctx->grid[s] = std::min(ctx->grid[s], ctx->nitems);
+  for (int s = 0; s < 6; ++s) ctx->grid[s] = std::min(ctx->grid[s], ctx->nitems);
   if (ctx->gexec) {
     cudaGraphExecDestroy(ctx->gexec);
     ctx->gexec = nullptr;
@@ -282,8 +284,9 @@ hbe_status ensure_graph(hbe_ctx *ctx) {
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
   hbe_status st = HBE_OK;
+  const int first = ctx->schedule ? 4 : 0, last = ctx->schedule ? 6 : 4;
   for (int k = 0; k < ctx->K && st == HBE_OK; ++k)
-    for (int s = 0; s < 4 && st == HBE_OK; ++s) {
+    for (int s = first; s < last && st == HBE_OK; ++s) {
       StageParams p{ctx->d_desc, ctx->d_items, ctx->d_nitems, ctx->d_err, k};
       st = launch_stage(ctx->err, vt.k[ctx->variant][s], ctx->grid[s], p, ctx->cap_stream);
     }
@@ -498,6 +501,7 @@ void hbe_destroy(hbe_ctx *ctx) {
   cudaFree(ctx->d_masks);
   cudaFree(ctx->d_labels);
   cudaFree(ctx->d_counts);
+  cudaFree(ctx->d_part);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
@@ -532,6 +536,22 @@ hbe_status hbe_variant_info(int prec, int variant, hbe_variant_t *out) {
     out->smem_bytes[s] = k[s].smem;
     out->ring[s] = k[s].ring;
   }
+  return HBE_OK;
+}
+
+hbe_status hbe_set_schedule(hbe_ctx *ctx, int schedule) {
+  if (!ctx) return HBE_EINVAL;
+  if (schedule != 0 && schedule != 1) return set_err(ctx->err, HBE_EINVAL, "schedule is 0 or 1");
+  if (ctx->in_batch) return set_err(ctx->err, HBE_ESTATE, "context is in a batch");
+  if (ctx->pending) {
+    hbe_status st = sync_ctx(ctx);
+    if (st != HBE_OK) return st;
+  }
+  if (ctx->schedule != schedule && ctx->gexec) {
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+  }
+  ctx->schedule = schedule;
   return HBE_OK;
 }
 
@@ -698,7 +718,7 @@ hbe_status hbe_step_async(hbe_ctx *ctx, int64_t nsteps, double dt) {
   }
   const int64_t runs = (nsteps + ctx->K - 1) / ctx->K;
   for (int64_t r = 0; r < runs; ++r) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
-  ctx->launches += runs * 4 * ctx->K;
+  ctx->launches += runs * (ctx->schedule ? 2 : 4) * ctx->K;
   ctx->pending = true;
   return HBE_OK;
 }
@@ -741,27 +761,29 @@ hbe_status hbe_profile_stages(hbe_ctx *ctx, int64_t nsteps, double dt, float *ms
     d.dt = dt;
   }
   CK(launch_set_run(ctx->d_desc, nsteps, d.t0, d.dt, d.stop_thr, 1, ctx->stream));
-  std::vector<cudaEvent_t> ev((size_t)nsteps * 5, nullptr);
+  const int first = ctx->schedule ? 4 : 0, nl = ctx->schedule ? 2 : 4;
+  std::vector<cudaEvent_t> ev((size_t)nsteps * (nl + 1), nullptr);
   for (auto &e : ev) CK(cudaEventCreate(&e));
   const VariantTable &vt = table_for(ctx->prec);
   for (int64_t n = 0; n < nsteps && st == HBE_OK; ++n) {
-    for (int s = 0; s < 4 && st == HBE_OK; ++s) {
-      CK(cudaEventRecord(ev[n * 5 + s], ctx->stream));
+    for (int s = 0; s < nl && st == HBE_OK; ++s) {
+      CK(cudaEventRecord(ev[n * (nl + 1) + s], ctx->stream));
       StageParams p{ctx->d_desc, ctx->d_items, ctx->d_nitems, ctx->d_err, 0};
-      st = launch_stage(ctx->err, vt.k[ctx->variant][s], ctx->grid[s], p, ctx->stream);
+      st = launch_stage(ctx->err, vt.k[ctx->variant][first + s], ctx->grid[first + s], p,
+                        ctx->stream);
     }
-    CK(cudaEventRecord(ev[n * 5 + 4], ctx->stream));
+    CK(cudaEventRecord(ev[n * (nl + 1) + nl], ctx->stream));
     CK(launch_advance(ctx->d_desc, ctx->d_one, 1, 1, ctx->stream));
   }
-  ctx->launches += nsteps * 4;
+  ctx->launches += nsteps * nl;
   ctx->pending = true;
   hbe_status st2 = sync_ctx(ctx);
   double acc[4] = {0, 0, 0, 0};
   if (st == HBE_OK && st2 == HBE_OK) {
     for (int64_t n = 0; n < nsteps; ++n)
-      for (int s = 0; s < 4; ++s) {
+      for (int s = 0; s < nl; ++s) {
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev[n * 5 + s], ev[n * 5 + s + 1]);
+        cudaEventElapsedTime(&ms, ev[n * (nl + 1) + s], ev[n * (nl + 1) + s + 1]);
         acc[s] += ms;
       }
   }
@@ -881,6 +903,37 @@ hbe_status hbe_diag(hbe_ctx *ctx, double eps, hbe_diag_t *out, uint32_t *pos_mas
   out->n_neg = (int64_t)c[2];
   const int64_t b = out->n_pos + out->n_neg - 1;
   out->bubble_count = b > 0 ? b : 0;
+  return HBE_OK;
+}
+
+hbe_status hbe_analysis(hbe_ctx *ctx, double eps, hbe_analysis_t *out) {
+  if (!ctx || !out) return HBE_EINVAL;
+  if (!ctx->has_state) return set_err(ctx->err, HBE_ESTATE, "no initial data");
+  if (!(eps >= 0.0)) return set_err(ctx->err, HBE_EINVAL, "eps must be >= 0");
+  hbe_status st = sync_ctx(ctx);
+  if (st != HBE_OK) return st;
+  const int nb = analysis_blocks();
+  if (!ctx->d_part) CK(cudaMalloc(&ctx->d_part, (5 * (size_t)nb + 5) * sizeof(double)));
+  const int sprec = ctx->prec == HBE_FP64 ? 0 : 1;
+  const bool kahan = is_kahan(ctx->prec);
+  const int set = (int)(ctx->h_desc->n_base & 1);
+  const double mcoef = 1.5 + std::sqrt(2.25 + ctx->mu * ctx->mu);
+  CK(launch_analysis(sprec, ctx->f[F_P0 + set], kahan ? ctx->f[F_PLO0 + set] : nullptr,
+                     ctx->f[F_Q0 + set], kahan ? ctx->f[F_QLO0 + set] : nullptr, ctx->N,
+                     ctx->pitch_s, ctx->hxs, ctx->bc, 1.0 / (ctx->h * ctx->h), mcoef, eps,
+                     ctx->d_part, ctx->d_part + 5 * (size_t)nb, ctx->stream));
+  double r[5];
+  CK(cudaMemcpyAsync(r, ctx->d_part + 5 * (size_t)nb, sizeof(r), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const double t = current_t(ctx);
+  const double h3 = ctx->h * ctx->h * ctx->h;
+  out->t = t;
+  out->integral_phi = r[0] * h3;
+  out->integral_phi3 = r[1] * h3;
+  out->laplacian_monitor = std::exp(-2.0 * t) * r[2];
+  out->support_points = (int64_t)r[3];
+  out->condition1_violations = (int64_t)r[4];
   return HBE_OK;
 }
 
@@ -1079,7 +1132,7 @@ static hbe_status batch_rebuild(hbe_batch *b) {
       if (!l.d_n) CKX(b->err, cudaMalloc(&l.d_n, sizeof(int)));
       CKX(b->err, cudaMalloc(&l.d_items, cap * sizeof(WorkItem)));
       l.cap = cap;
-      for (int s = 0; s < 4; ++s) {
+      for (int s = 0; s < 6; ++s) {
         hbe_status st = persistent_grid(b->err, vt.k[v][s], b->sms, &l.grid[s]);
         if (st != HBE_OK) return st;
       }
@@ -1101,8 +1154,9 @@ static hbe_status batch_rebuild(hbe_batch *b) {
     cudaGraph_t g = nullptr;
     CKX(b->err, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     hbe_status st = HBE_OK;
+    // the batch always runs the fused stage pairs (kernels 4 and 5 of a variant)
     for (int k = 0; k < b->K && st == HBE_OK; ++k)
-      for (int s = 0; s < 4 && st == HBE_OK; ++s)
+      for (int s = 4; s < 6 && st == HBE_OK; ++s)
         for (int v = 0; v < b->nvariants && st == HBE_OK; ++v) {
           auto &l = b->lists[v];
           if (!l.d_n) continue;
@@ -1134,7 +1188,7 @@ hbe_status hbe_batch_run(hbe_batch *b, hbe_ctx **finished, int max_finished, int
   CKX(b->err, cudaGraphLaunch(b->gexec, b->stream));
   int used = 0;
   for (int v = 0; v < b->nvariants; ++v) used += b->lists[v].d_n ? 1 : 0;
-  b->launches += (int64_t)4 * b->K * used;
+  b->launches += (int64_t)2 * b->K * used;
   CKX(b->err, cudaMemcpyAsync(b->h_descs, b->d_descs, M * sizeof(Desc), cudaMemcpyDeviceToHost,
                               b->stream));
   CKX(b->err, cudaStreamSynchronize(b->stream));
@@ -1145,7 +1199,7 @@ hbe_status hbe_batch_run(hbe_batch *b, hbe_ctx **finished, int max_finished, int
   for (int i = 0; i < M; ++i) {
     hbe_ctx *c = b->members[i];
     *c->h_desc = b->h_descs[i];
-    c->launches += (int64_t)4 * b->K;
+    c->launches += (int64_t)2 * b->K;
     const Desc &d = b->h_descs[i];
     if (d.n_base >= d.n_end || d.status != ST_RUNNING) {
       leave_batch(c);

@@ -332,4 +332,104 @@ cudaError_t launch_ccl(const uint32_t *mask, int N, int periodic, int *labels,
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- analysis
+// Per-block partial reductions of the paper's analysis quantities over the
+// N^3 unknowns of the current state (double precision):
+//   [0] sum phi, [1] sum phi^3, [2] max |FD4 Laplacian of phi| (as double bits),
+//   [3] points with |phi| + |psi| > eps ("support"), [4] support points where
+//   m phi + psi >= 0 (the first bubble condition fails), m = 3/2 + sqrt(9/4 + mu^2).
+// A second single-block pass adds the partials in a fixed order, so the
+// result does not depend on scheduling.
+template <class T>
+__global__ void analysis_kernel(const T *__restrict__ phi, const T *__restrict__ phlo,
+                                const T *__restrict__ psi, const T *__restrict__ pslo, int N,
+                                int pitch, int hx, int periodic, double inv_h2, double mcoef,
+                                double eps, double *__restrict__ part) {
+  const int64_t plane = (int64_t)(N + 4) * pitch;
+  const int64_t n3 = (int64_t)N * N * N;
+  double s1 = 0.0, s3 = 0.0, lmax = 0.0, sup = 0.0, bad = 0.0;
+  auto at = [&](int x, int y, int z) -> double {
+    // padded layout: x and y ghosts are stored (0 or wrapped); z wraps or reads 0
+    if (z < 0 || z >= N) {
+      if (!periodic) return 0.0;
+      z = (z + N) % N;
+    }
+    const int64_t o = (int64_t)z * plane + (int64_t)(y + 2) * pitch + x + hx;
+    double v = (double)phi[o];
+    if (phlo) v += (double)phlo[o];
+    return v;
+  };
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % N);
+    const int64_t r = i / N;
+    const int y = (int)(r % N), z = (int)(r / N);
+    const double c = at(x, y, z);
+    const int64_t o = (int64_t)z * plane + (int64_t)(y + 2) * pitch + x + hx;
+    double q = (double)psi[o];
+    if (pslo) q += (double)pslo[o];
+    double lap = 0.0;
+    lap += -1.0 / 12.0 * (at(x - 2, y, z) + at(x + 2, y, z)) + 4.0 / 3.0 * (at(x - 1, y, z) + at(x + 1, y, z)) - 2.5 * c;
+    lap += -1.0 / 12.0 * (at(x, y - 2, z) + at(x, y + 2, z)) + 4.0 / 3.0 * (at(x, y - 1, z) + at(x, y + 1, z)) - 2.5 * c;
+    lap += -1.0 / 12.0 * (at(x, y, z - 2) + at(x, y, z + 2)) + 4.0 / 3.0 * (at(x, y, z - 1) + at(x, y, z + 1)) - 2.5 * c;
+    lap = fabs(lap * inv_h2);
+    s1 += c;
+    s3 += c * c * c;
+    lmax = (lap <= lmax) ? lmax : ((lap == lap) ? lap : (double)INFINITY);
+    if (fabs(c) + fabs(q) > eps) {
+      sup += 1.0;
+      if (mcoef * c + q >= 0.0) bad += 1.0;
+    }
+  }
+  __shared__ double red[5][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+    lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    sup += __shfl_xor_sync(0xffffffffu, sup, o);
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if (lane == 0) { red[0][wid] = s1; red[1][wid] = s3; red[2][wid] = lmax; red[3][wid] = sup; red[4][wid] = bad; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a[5] = {0, 0, 0, 0, 0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a[0] += red[0][w]; a[1] += red[1][w]; a[2] = fmax(a[2], red[2][w]);
+      a[3] += red[3][w]; a[4] += red[4][w];
+    }
+    for (int k = 0; k < 5; ++k) part[(int64_t)k * gridDim.x + blockIdx.x] = a[k];
+  }
+}
+
+__global__ void analysis_finish_kernel(const double *part, int nblocks, double *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a[5] = {0, 0, 0, 0, 0};
+  for (int b = 0; b < nblocks; ++b) {
+    a[0] += part[b]; a[1] += part[nblocks + b]; a[2] = fmax(a[2], part[2 * nblocks + b]);
+    a[3] += part[3 * nblocks + b]; a[4] += part[4 * nblocks + b];
+  }
+  for (int k = 0; k < 5; ++k) out[k] = a[k];
+}
+
+int analysis_blocks() { return 152 * 4; }
+
+cudaError_t launch_analysis(int prec, const void *phi, const void *phlo, const void *psi,
+                            const void *pslo, int N, int pitch, int hx, int periodic,
+                            double inv_h2, double mcoef, double eps, double *part, double *out,
+                            cudaStream_t st) {
+  const int blocks = analysis_blocks();
+  if (prec == 0)
+    analysis_kernel<double><<<blocks, 256, 0, st>>>((const double *)phi, (const double *)phlo,
+                                                    (const double *)psi, (const double *)pslo, N,
+                                                    pitch, hx, periodic, inv_h2, mcoef, eps, part);
+  else
+    analysis_kernel<float><<<blocks, 256, 0, st>>>((const float *)phi, (const float *)phlo,
+                                                   (const float *)psi, (const float *)pslo, N,
+                                                   pitch, hx, periodic, inv_h2, mcoef, eps, part);
+  analysis_finish_kernel<<<1, 32, 0, st>>>(part, blocks, out);
+  return cudaGetLastError();
+}
+
 }  // namespace hbe

@@ -20,4 +20,10 @@ cudaError_t launch_signpack(int prec, const void *hi, const void *lo, int N, int
 cudaError_t launch_ccl(const uint32_t *mask, int N, int periodic, int *labels,
                        unsigned long long *count, unsigned *err, cudaStream_t st);
 
+int analysis_blocks();
+cudaError_t launch_analysis(int prec, const void *phi, const void *phlo, const void *psi,
+                            const void *pslo, int N, int pitch, int hx, int periodic,
+                            double inv_h2, double mcoef, double eps, double *part, double *out,
+                            cudaStream_t st);
+
 }  // namespace hbe

@@ -35,6 +35,8 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "hbe_common.cuh"
 
 namespace hbe {
@@ -252,13 +254,6 @@ __device__ __forceinline__ void store_point(T *row, int64_t pitch, int N, bool r
   }
 }
 
-// Coefficients of one stage, formed in double precision by one thread.
-template <class TM>
-struct Coef {
-  TM c43, cm12, ccen, nlam, a1, a2, m3;   // stencil / combine
-  TM b6, d6;                              // stage-4 combine
-};
-
 // ---------------------------------------------------------------- the kernel
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
@@ -279,28 +274,6 @@ __device__ __forceinline__ bool item_active(Desc *d, int k, bool leader) {
     }
   }
   return true;
-}
-
-// Stage coefficients in double precision, narrowed to the math type.
-template <class C>
-__device__ __forceinline__ Coef<typename C::TM> stage_coef(const Desc *d, long long n) {
-  using TM = typename C::TM;
-  constexpr int S = C::S;
-  const double dt = d->dt;
-  const double tn = d->t0 + (double)n * dt;
-  const double ts = tn + (S == 1 ? 0.0 : (S == 4 ? dt : 0.5 * dt));
-  const double c = exp(-2.0 * ts) * d->inv_h2;
-  Coef<TM> cf;
-  cf.c43 = (TM)(4.0 / 3.0 * c);
-  cf.cm12 = (TM)(-c / 12.0);
-  cf.ccen = C::DIFF ? (TM)d->mu2 : (TM)(d->mu2 - 7.5 * c);
-  cf.nlam = (TM)(-d->lambda);
-  cf.m3 = (TM)(-3.0);
-  cf.a1 = (TM)(S == 1 ? 0.0 : (S == 4 ? dt : 0.5 * dt));
-  cf.a2 = (TM)(S == 3 ? 0.25 * dt * dt : (S == 4 ? 0.5 * dt * dt : 0.0));
-  cf.b6 = (TM)(dt * dt / 6.0);
-  cf.d6 = (TM)(dt / 6.0);
-  return cf;
 }
 
 template <class TM>
@@ -386,360 +359,51 @@ __device__ __forceinline__ void produce(const StageParams &prm, uint64_t *full, 
 }
 
 // ---------------------------------------------------------------- consumer warps
-template <class C>
-struct Consumer {
-  using TS = typename C::TS;
-  using TG = typename C::TG;
-  using TM = typename C::TM;
-  static constexpr int S = C::S, VEC = C::VEC, VY = C::VY, TX = C::TX;
-  static constexpr int BXS = C::BXS, BXG = C::BXG, HXS = C::HXS, HXG = C::HXG;
-  static constexpr int NI = C::NIS + C::NIG;  // point-only input fields
-
-  // Stage argument P at n consecutive tile positions from (lx, ly) (ly in
-  // [-2, TY+2)), formed from the ring tiles.
-  template <int n>
-  static __device__ __forceinline__ void comb_n(const unsigned char *base, const Coef<TM> &cf,
-                                                int lx, int ly, TM (&out)[n]) {
-    load_as<TS, TM, n>(reinterpret_cast<const TS *>(base) + (ly + 2) * BXS + lx + HXS, out);
-    if constexpr (S >= 2) {
-      TM qv[n];
-      load_as<TS, TM, n>(reinterpret_cast<const TS *>(base + C::HS_BYTES) + (ly + 2) * BXS + lx + HXS, qv);
-#pragma unroll
-      for (int j = 0; j < n; ++j) out[j] = fmaT(cf.a1, qv[j], out[j]);
-    }
-    if constexpr (S >= 3) {
-      TM gv[n];
-      load_as<TG, TM, n>(reinterpret_cast<const TG *>(base + C::OFF_HG) + (ly + 2) * BXG + lx + HXG, gv);
-#pragma unroll
-      for (int j = 0; j < n; ++j) out[j] = fmaT(cf.a2, gv[j], out[j]);
-    }
-  }
-  static __device__ __forceinline__ void comb(const unsigned char *base, const Coef<TM> &cf,
-                                              int lx, int ly, TM (&out)[VEC]) {
-    comb_n<VEC>(base, cf, lx, ly, out);
-  }
-
-  // x neighbours (x-2, x-1, x+1, x+2) of the lane's VEC points in tile row ly,
-  // whose own P values are c.
-  static __device__ __forceinline__ void xnb(const unsigned char *base, const Coef<TM> &cf,
-                                             int lane, int lx0, int ly, const TM (&c)[VEC],
-                                             TM (&m2)[VEC], TM (&m1)[VEC], TM (&p1)[VEC],
-                                             TM (&p2)[VEC]) {
-    if constexpr (S == 1) {
-      // P = p: read the neighbours straight from the halo tile
-      const TS *hp = reinterpret_cast<const TS *>(base) + (ly + 2) * BXS + lx0 + HXS;
-      if constexpr (VEC == 4) {
-        TM a[4], b[4];
-        load_as<TS, TM, 4>(hp - 4, a);
-        load_as<TS, TM, 4>(hp + 4, b);
-        const TM e[8] = {a[2], a[3], c[0], c[1], c[2], c[3], b[0], b[1]};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          m2[j] = e[j]; m1[j] = e[j + 1]; p1[j] = e[j + 3]; p2[j] = e[j + 4];
-        }
-      } else if constexpr (VEC == 2) {
-        TM a[2], b[2];
-        load_as<TS, TM, 2>(hp - 2, a);
-        load_as<TS, TM, 2>(hp + 2, b);
-        m2[0] = a[0]; m1[0] = a[1]; p1[0] = c[1]; p2[0] = b[0];
-        m2[1] = a[1]; m1[1] = c[0]; p1[1] = b[0]; p2[1] = b[1];
-      } else {
-        m2[0] = (TM)hp[-2]; m1[0] = (TM)hp[-1]; p1[0] = (TM)hp[1]; p2[0] = (TM)hp[2];
-      }
-    } else if constexpr (VEC == 4) {
-      // the two points each side come from the neighbouring lanes, or from the
-      // halo columns for the first and last lane
-      TM pc = shfl_up1(c[2], 1), pd = shfl_up1(c[3], 1);
-      TM na = shfl_dn1(c[0], 1), nb = shfl_dn1(c[1], 1);
-      if (lane == 0) {
-        TM hv[2];
-        Consumer::template comb_n<2>(base, cf, -2, ly, hv);
-        pc = hv[0]; pd = hv[1];
-      } else if (lane == 31) {
-        TM hv[2];
-        Consumer::template comb_n<2>(base, cf, TX, ly, hv);
-        na = hv[0]; nb = hv[1];
-      }
-      const TM e[8] = {pc, pd, c[0], c[1], c[2], c[3], na, nb};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        m2[j] = e[j]; m1[j] = e[j + 1]; p1[j] = e[j + 3]; p2[j] = e[j + 4];
-      }
-    } else if constexpr (VEC == 2) {
-      TM pa = shfl_up1(c[0], 1), pb = shfl_up1(c[1], 1);
-      TM na = shfl_dn1(c[0], 1), nb = shfl_dn1(c[1], 1);
-      if (lane == 0) {
-        TM hv[2];
-        comb(base, cf, -2, ly, hv);
-        pa = hv[0]; pb = hv[1];
-      } else if (lane == 31) {
-        TM hv[2];
-        comb(base, cf, TX, ly, hv);
-        na = hv[0]; nb = hv[1];
-      }
-      m2[0] = pa; m1[0] = pb; p1[0] = c[1]; p2[0] = na;
-      m2[1] = pb; m1[1] = c[0]; p1[1] = na; p2[1] = nb;
-    } else {
-      TM hv[1] = {c[0]};
-      if (lane < 2) comb(base, cf, lane - 2, ly, hv);
-      else if (lane >= 30) comb(base, cf, TX + lane - 30, ly, hv);
-      const TM up2 = shfl_up1(c[0], 2), up1 = shfl_up1(c[0], 1);
-      const TM dn2 = shfl_dn1(c[0], 2), dn1 = shfl_dn1(c[0], 1);
-      const TM h1 = shfl_idx(hv[0], 1), h30 = shfl_idx(hv[0], 30);
-      m2[0] = lane < 2 ? hv[0] : up2;
-      m1[0] = lane == 0 ? h1 : up1;
-      p2[0] = lane >= 30 ? hv[0] : dn2;
-      p1[0] = lane == 31 ? h30 : dn1;
-    }
-  }
-
-  static __device__ __forceinline__ TM lap_g(const Coef<TM> &cf, TM P0, TM xm2, TM xm1, TM xp1,
-                                             TM xp2, TM ym2, TM ym1, TM yp1, TM yp2, TM zm2,
-                                             TM zm1, TM zp1, TM zp2, TM Q) {
-    TM s1, s2;
-    if constexpr (C::DIFF) {
-      s1 = ((xm1 - P0) + (xp1 - P0)) + (((ym1 - P0) + (yp1 - P0)) + ((zm1 - P0) + (zp1 - P0)));
-      s2 = ((xm2 - P0) + (xp2 - P0)) + (((ym2 - P0) + (yp2 - P0)) + ((zm2 - P0) + (zp2 - P0)));
-    } else {
-      s1 = ((xm1 + xp1) + (ym1 + yp1)) + (zm1 + zp1);
-      s2 = ((xm2 + xp2) + (ym2 + yp2)) + (zm2 + zp2);
-    }
-    TM g = fmaT(cf.nlam * (P0 * P0), P0, cf.m3 * Q);
-    g = fmaT(cf.ccen, P0, g);
-    g = fmaT(cf.cm12, s2, g);
-    return fmaT(cf.c43, s1, g);
-  }
-
-  static __device__ __forceinline__ void run(const StageParams &prm, uint64_t *full,
-                                             uint64_t *empty, const unsigned char *ring,
-                                             volatile int *abort_flag, int warp, int lane) {
-    constexpr int RING = C::RING;
-    const int nitems = *prm.nitems;
-    const int lx0 = lane * VEC, ly0 = warp * VY;
-    int slot = 0;
-    uint32_t phase = 0;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-      const WorkItem w = prm.items[it];
-      Desc *d = prm.descs + w.x;
-      if (!item_active<S>(d, prm.k, warp == 0 && lane == 0)) continue;
-      const long long n = d->n_base + prm.k;
-      Coef<TM> cf;
-      {
-        Coef<TM> c0;
-        if (lane == 0) c0 = stage_coef<C>(d, n);
-        const TM *src = reinterpret_cast<const TM *>(&c0);
-        TM *dst = reinterpret_cast<TM *>(&cf);
-#pragma unroll
-        for (int i = 0; i < (int)(sizeof(Coef<TM>) / sizeof(TM)); ++i) dst[i] = shfl_idx(src[i], 0);
-      }
-      // ---- everything the item needs from the descriptor, held in registers
-      const int N = d->N;
-      const bool periodic = d->bc == 1;
-      const int set = (int)(n & 1);
-      const int so = set ^ 1;
-      const int x0 = (w.y & 0xffff) * TX, y0 = (w.y >> 16) * C::TY;
-      const int z0 = w.z, len = w.w, nplanes = len + 4;
-      const bool ragged = x0 + TX > N;
-      const int x = x0 + lx0;
-      // periodic ghost copies are written only by the lanes / rows next to a wrap
-      const bool lane_edge = periodic && (x < 2 || x + VEC > N - 2);
-      const int64_t pitch_s = d->pitch_s, plane_s = d->plane_s;
-      const int64_t pitch_g = d->pitch_g, plane_g = d->plane_g;
-      const int64_t row_s = (int64_t)(y0 + ly0 + 2) * pitch_s + HXS + x;  // row r: + r pitch
-      const int64_t row_g = (int64_t)(y0 + ly0 + 2) * pitch_g + HXG + x;
-      const bool xok = x < N;
-      (void)len;
-      // outputs
-      TG *outG = nullptr;
-      TS *outP = nullptr, *outQ = nullptr, *outPL = nullptr, *outQL = nullptr;
-      if constexpr (S <= 3) outG = reinterpret_cast<TG *>(d->f[S == 1 ? F_G1 : (S == 2 ? F_G2 : F_G3)]);
-      if constexpr (S == 4) {
-        outP = reinterpret_cast<TS *>(d->f[F_P0 + so]);
-        outQ = reinterpret_cast<TS *>(d->f[F_Q0 + so]);
-        if constexpr (C::KAHAN) {
-          outPL = reinterpret_cast<TS *>(d->f[F_PLO0 + so]);
-          outQL = reinterpret_cast<TS *>(d->f[F_QLO0 + so]);
-        }
-      }
-      bool rok[VY];
-#pragma unroll
-      for (int r = 0; r < VY; ++r) rok[r] = xok && (y0 + ly0 + r < N);
-
-      TM win[5][VY][VEC];
-#pragma unroll
-      for (int a = 0; a < 5; ++a)
-#pragma unroll
-        for (int r = 0; r < VY; ++r)
-#pragma unroll
-          for (int j = 0; j < VEC; ++j) win[a][r][j] = (TM)0;
-      TM run_max = (TM)0;
-
-      for (int m = 0; m < nplanes; ++m) {
-        if (!mbar_wait_bounded(&full[slot], phase)) {
-          *abort_flag = 1;
-          atomicOr(prm.err, (unsigned)DEV_ERR_TIMEOUT);
-          return;
-        }
-        if (*abort_flag) return;
-        const unsigned char *base = ring + slot * C::SLOT_BYTES;
-        // own rows at plane z0 - 2 + m enter the window
-#pragma unroll
-        for (int r = 0; r < VY; ++r) {
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) win[a][r][j] = win[a + 1][r][j];
-          comb(base, cf, lx0, ly0 + r, win[4][r]);
-        }
-        const int s2 = slot >= 2 ? slot - 2 : slot + RING - 2;  // slot of plane m - 2
-        if (m >= 4) {
-          // ---- output plane z0 + m - 4, loaded as plane m - 2
-          const int z = z0 + m - 4;
-          const unsigned char *b2 = ring + s2 * C::SLOT_BYTES;
-          TM R[VY + 4][VEC];  // rows ly0-2 .. ly0+VY+1 of P at plane z
-          comb(b2, cf, lx0, ly0 - 2, R[0]);
-          comb(b2, cf, lx0, ly0 - 1, R[1]);
-          comb(b2, cf, lx0, ly0 + VY, R[VY + 2]);
-          comb(b2, cf, lx0, ly0 + VY + 1, R[VY + 3]);
-#pragma unroll
-          for (int r = 0; r < VY; ++r)
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) R[r + 2][j] = win[2][r][j];
-#pragma unroll
-          for (int r = 0; r < VY; ++r) {
-            const int ly = ly0 + r;
-            const int y = y0 + ly;
-            TM m2[VEC], m1[VEC], p1[VEC], p2[VEC];
-            xnb(b2, cf, lane, lx0, ly, win[2][r], m2, m1, p1, p2);
-            const int hoff = (ly + 2) * BXS + lx0 + HXS;
-            const int ioff = ly * TX + lx0;
-            // point-only inputs from the interior tiles
-            TM cur[NI > 0 ? NI : 1][VEC];
-            if constexpr (S == 1) {
-              load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(b2 + C::OFF_IS) + ioff, cur[0]);
-            } else {
-              const TG *ig = reinterpret_cast<const TG *>(b2 + C::OFF_IG) + ioff;
-              load_as<TG, TM, VEC>(ig, cur[0]);  // S2: G1, S3: G2, S4: G1
-              if constexpr (S == 4) {
-                load_as<TG, TM, VEC>(ig + C::IG_BYTES / (int)sizeof(TG), cur[1]);  // G3
-                if constexpr (C::KAHAN) {
-                  const TS *is = reinterpret_cast<const TS *>(b2 + C::OFF_IS) + ioff;
-                  load_as<TS, TM, VEC>(is, cur[2]);
-                  load_as<TS, TM, VEC>(is + C::IS_BYTES / (int)sizeof(TS), cur[3]);
-                }
-              }
-            }
-            TM Q[VEC], qS[VEC];
-            if constexpr (S == 1) {
-#pragma unroll
-              for (int j = 0; j < VEC; ++j) Q[j] = cur[0][j];
-            } else {
-              load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(b2 + C::HS_BYTES) + hoff, qS);
-              // S2: q + dt/2 G1, S3: q + dt/2 G2, S4: q + dt G3
-              const int gi = (S == 4) ? 1 : 0;
-#pragma unroll
-              for (int j = 0; j < VEC; ++j) Q[j] = fmaT(cf.a1, cur[gi][j], qS[j]);
-            }
-            TM Gout[VEC];
-#pragma unroll
-            for (int j = 0; j < VEC; ++j)
-              Gout[j] = lap_g(cf, win[2][r][j], m2[j], m1[j], p1[j], p2[j], R[r][j], R[r + 1][j],
-                              R[r + 3][j], R[r + 4][j], win[0][r][j], win[1][r][j], win[3][r][j],
-                              win[4][r][j], Q[j]);
-            if (!rok[r]) continue;
-            const bool edge = lane_edge || (periodic && (y < 2 || y >= N - 2));
-            if constexpr (S <= 3) {
-              TG *row = outG + ((int64_t)z * plane_g + row_g + r * pitch_g - x);
-              store_point<TG, TM, VEC>(row, pitch_g, N, ragged, edge, x, y, Gout);
-            } else {
-              // RK4 combine (Sec. 2.1): p' = p + dt q + dt^2/6 (G1 + G2 + G3),
-              //                         q' = q + dt/6 (G1 + 2 G2 + 2 G3 + G4)
-              TM pS[VEC], G2h[VEC];
-              load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(b2) + hoff, pS);
-              load_as<TG, TM, VEC>(reinterpret_cast<const TG *>(b2 + C::OFF_HG) +
-                                       (ly + 2) * BXG + lx0 + HXG, G2h);
-              TM pn[VEC], qn[VEC], pl[VEC], ql[VEC];
-#pragma unroll
-              for (int j = 0; j < VEC; ++j) {
-                const TM g1 = cur[0][j], g3 = cur[1][j];
-                const TM dp = fmaT(cf.b6, (g1 + G2h[j]) + g3, cf.a1 * qS[j]);
-                const TM dq = cf.d6 * ((g1 + Gout[j]) + (TM)2 * (G2h[j] + g3));
-                if constexpr (C::KAHAN) {
-                  two_sum(pS[j], dp + cur[2][j], pn[j], pl[j]);
-                  two_sum(qS[j], dq + cur[3][j], qn[j], ql[j]);
-                } else {
-                  pn[j] = pS[j] + dp;
-                  qn[j] = qS[j] + dq;
-                }
-                if (x + j < N) {
-                  const TM a = pn[j] < (TM)0 ? -pn[j] : pn[j];
-                  // NaN and overflow both read as +inf in the running max
-                  run_max = (a <= run_max) ? run_max : ((a == a) ? a : (TM)INFINITY);
-                }
-              }
-              const int64_t off = (int64_t)z * plane_s + row_s + r * pitch_s - x;
-              store_point<TS, TM, VEC>(outP + off, pitch_s, N, ragged, edge, x, y, pn);
-              store_point<TS, TM, VEC>(outQ + off, pitch_s, N, ragged, edge, x, y, qn);
-              if constexpr (C::KAHAN) {
-                store_point<TS, TM, VEC>(outPL + off, pitch_s, N, ragged, edge, x, y, pl);
-                store_point<TS, TM, VEC>(outQL + off, pitch_s, N, ragged, edge, x, y, ql);
-              }
-            }
-          }
-        }
-        // release the slots this warp no longer needs
-        __syncwarp();
-        if (lane == 0) {
-          if (m < 2 || m >= nplanes - 2) mbar_arrive(&empty[slot]);
-          if (m >= 4) mbar_arrive(&empty[s2]);
-        }
-        if (++slot == RING) { slot = 0; phase ^= 1u; }
-      }
-      if constexpr (S == 4) {
-        double v = (double)run_max;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (lane == 0) atomicMax(d->maxabs + prm.k, (unsigned long long)__double_as_longlong(v));
-      }
-    }
-  }
-};
-
-// Coefficients of a fused pair of stages, formed in double precision.
+// Coefficients of the stage(s) one launch evaluates, formed in double
+// precision.  Kind k = 0 (and 1 for a fused pair) is one RK stage:
+//   stage argument  P_k = p + kq[k] q + kg[k] G(tile k),
+//   stencil         c43[k], cm12[k], ccen[k],
+//   point argument  Q_0 = q + q0 X (X = the stage's G input, or 0),
+//                   Q_1 = q + q1 * (result of kind 0).
 template <class TM>
-struct PairCoef {
-  TM c43a, cm12a, ccena;  // stencil coefficients of the first stage of the pair
-  TM c43b, cm12b, ccenb;  // and of the second
+struct UCoef {
+  TM c43[2], cm12[2], ccen[2];
+  TM kq[2], kg[2];
+  TM q0, q1;
   TM nlam, m3;
-  TM aq, ag;              // Pa = p + aq q + ag G1          (pair 3+4)
-  TM bq, bg;              // Pb = p + bq q + bg G2          (pair 1+2: bg = 0)
-  TM qa;                  // Qa = q + qa G2                 (pair 3+4)
-  TM qb;                  // Qb = q + qb * (first stage's G)
-  TM b6, d6, dt;          // RK4 combine (pair 3+4)
+  TM b6, d6, dt;
 };
 
 template <class C>
-__device__ __forceinline__ PairCoef<typename C::TM> pair_coef(const Desc *d, long long n) {
+__device__ __forceinline__ UCoef<typename C::TM> unified_coef(const Desc *d, long long n) {
   using TM = typename C::TM;
-  const bool second = C::S == 6;
+  constexpr int S = C::S;
   const double dt = d->dt;
   const double tn = d->t0 + (double)n * dt;
-  const double ta = second ? tn + 0.5 * dt : tn;        // stage 3 | stage 1
-  const double tb = second ? tn + dt : tn + 0.5 * dt;   // stage 4 | stage 2
-  const double ca = exp(-2.0 * ta) * d->inv_h2, cb = exp(-2.0 * tb) * d->inv_h2;
-  PairCoef<TM> k;
-  k.c43a = (TM)(4.0 / 3.0 * ca); k.cm12a = (TM)(-ca / 12.0);
-  k.ccena = C::DIFF ? (TM)d->mu2 : (TM)(d->mu2 - 7.5 * ca);
-  k.c43b = (TM)(4.0 / 3.0 * cb); k.cm12b = (TM)(-cb / 12.0);
-  k.ccenb = C::DIFF ? (TM)d->mu2 : (TM)(d->mu2 - 7.5 * cb);
+  // stage times t, t + dt/2, t + dt/2, t + dt of stages 1..4
+  const double st[4] = {tn, tn + 0.5 * dt, tn + 0.5 * dt, tn + dt};
+  const int s0 = S <= 4 ? S - 1 : (S == 5 ? 0 : 2);  // stage of kind 0
+  UCoef<TM> k;
+  for (int i = 0; i < 2; ++i) {
+    const double c = exp(-2.0 * st[(s0 + i) & 3]) * d->inv_h2;
+    k.c43[i] = (TM)(4.0 / 3.0 * c);
+    k.cm12[i] = (TM)(-c / 12.0);
+    k.ccen[i] = C::DIFF ? (TM)d->mu2 : (TM)(d->mu2 - 7.5 * c);
+  }
+  // stage arguments: stage 1 p; stage 2 p + dt/2 q; stage 3 p + dt/2 q + dt^2/4 G1;
+  // stage 4 p + dt q + dt^2/2 G2
+  const double sq[4] = {0.0, 0.5 * dt, 0.5 * dt, dt};
+  const double sg[4] = {0.0, 0.0, 0.25 * dt * dt, 0.5 * dt * dt};
+  // point arguments: stage 2 q + dt/2 G1; stage 3 q + dt/2 G2; stage 4 q + dt G3
+  const double sp[4] = {0.0, 0.5 * dt, 0.5 * dt, dt};
+  for (int i = 0; i < 2; ++i) {
+    k.kq[i] = (TM)sq[(s0 + i) & 3];
+    k.kg[i] = (TM)sg[(s0 + i) & 3];
+  }
+  k.q0 = (TM)sp[s0];
+  k.q1 = (TM)sp[(s0 + 1) & 3];
   k.nlam = (TM)(-d->lambda);
   k.m3 = (TM)(-3.0);
-  k.aq = (TM)(second ? 0.5 * dt : 0.0);
-  k.ag = (TM)(second ? 0.25 * dt * dt : 0.0);
-  k.bq = (TM)(second ? dt : 0.5 * dt);
-  k.bg = (TM)(second ? 0.5 * dt * dt : 0.0);
-  k.qa = (TM)(second ? 0.5 * dt : 0.0);
-  k.qb = (TM)(second ? dt : 0.5 * dt);
   k.b6 = (TM)(dt * dt / 6.0);
   k.d6 = (TM)(dt / 6.0);
   k.dt = (TM)dt;
@@ -747,9 +411,9 @@ __device__ __forceinline__ PairCoef<typename C::TM> pair_coef(const Desc *d, lon
 }
 
 template <class TM>
-__device__ __forceinline__ TM lap_g2(TM c43, TM cm12, TM ccen, TM nlam, TM m3, bool diff, TM P0,
-                                     TM xm2, TM xm1, TM xp1, TM xp2, TM ym2, TM ym1, TM yp1,
-                                     TM yp2, TM zm2, TM zm1, TM zp1, TM zp2, TM Q) {
+__device__ __forceinline__ TM lap_g(TM c43, TM cm12, TM ccen, TM nlam, TM m3, bool diff, TM P0,
+                                    TM xm2, TM xm1, TM xp1, TM xp2, TM ym2, TM ym1, TM yp1,
+                                    TM yp2, TM zm2, TM zm1, TM zp1, TM zp2, TM Q) {
   TM s1, s2;
   if (diff) {
     s1 = ((xm1 - P0) + (xp1 - P0)) + (((ym1 - P0) + (yp1 - P0)) + ((zm1 - P0) + (zp1 - P0)));
@@ -764,263 +428,389 @@ __device__ __forceinline__ TM lap_g2(TM c43, TM cm12, TM ccen, TM nlam, TM m3, b
   return fmaT(c43, s1, g);
 }
 
-// Two RK stages per launch.  Pair 1+2: G1 = G(t, p, q) and
-// G2 = G(t + dt/2, p + dt/2 q, q + dt/2 G1) need p and q (with halo) only, and
-// G1 enters G2 at the point.  Pair 3+4: G3 = G(t + dt/2, p + dt/2 q + dt^2/4 G1,
-// q + dt/2 G2) and G4 = G(t + dt, p + dt q + dt^2/2 G2, q + dt G3) need p, q,
-// G1, G2 (with halo) and G3 only at the point, so G3 never leaves the SM; the
-// RK4 combine follows.  Both stage arguments of a pair are formed from the same
-// ring tiles.
+// One consumer warp.  Kinds (KN = 1 for one stage, 2 for a fused pair) share
+// the ring tiles; the register window holds P of every kind at planes
+// z-2..z+2 for the warp's own points, indexed by plane number mod 5 so that the
+// unrolled plane loop never moves registers.
 template <class C>
-struct PairConsumer {
+struct Consumer {
   using TS = typename C::TS;
   using TG = typename C::TG;
   using TM = typename C::TM;
-  static constexpr int S = C::S, VEC = C::VEC, VY = C::VY, TX = C::TX;
+  static constexpr int S = C::S, VEC = C::VEC, VY = C::VY, TX = C::TX, RING = C::RING;
   static constexpr int BXS = C::BXS, BXG = C::BXG, HXS = C::HXS, HXG = C::HXG;
+  static constexpr int KN = C::PAIR ? 2 : 1;
 
-  // Both stage arguments at n consecutive positions from (lx, ly).
+  // G tile (halo) that enters the stage argument of kind k, or -1
+  __host__ __device__ static constexpr int gtile(int kk) {
+    return (S == 3 || S == 4) ? (kk == 0 ? 0 : -1) : (S == 6 ? kk : -1);
+  }
+  __host__ __device__ static constexpr bool uses_q(int kk) { return !(S == 1 || (S == 5 && kk == 0)); }
+
+  const unsigned char *ring;
+  UCoef<TM> k;
+  int lane, lx0, ly0;
+
+  // Stage arguments of every kind at n consecutive tile positions from (lx, ly).
   template <int n>
-  static __device__ __forceinline__ void comb2(const unsigned char *base, const PairCoef<TM> &k,
-                                               int lx, int ly, TM (&pa)[n], TM (&pb)[n]) {
-    TM pv[n], qv[n];
+  __device__ __forceinline__ void comb(const unsigned char *base, int lx, int ly,
+                                       TM (&out)[KN][n]) const {
+    TM pv[n], qv[n] = {};
     load_as<TS, TM, n>(reinterpret_cast<const TS *>(base) + (ly + 2) * BXS + lx + HXS, pv);
-    load_as<TS, TM, n>(reinterpret_cast<const TS *>(base + C::HS_BYTES) + (ly + 2) * BXS + lx + HXS, qv);
-    if constexpr (S == 5) {
+    if constexpr (uses_q(0) || (KN == 2 && uses_q(1)))
+      load_as<TS, TM, n>(reinterpret_cast<const TS *>(base + C::HS_BYTES) + (ly + 2) * BXS + lx + HXS, qv);
 #pragma unroll
-      for (int j = 0; j < n; ++j) { pa[j] = pv[j]; pb[j] = fmaT(k.bq, qv[j], pv[j]); }
-    } else {
-      TM g1[n], g2[n];
-      const TG *hg = reinterpret_cast<const TG *>(base + C::OFF_HG) + (ly + 2) * BXG + lx + HXG;
-      load_as<TG, TM, n>(hg, g1);
-      load_as<TG, TM, n>(hg + C::HG_BYTES / (int)sizeof(TG), g2);
+    for (int kk = 0; kk < KN; ++kk) {
+      TM gv[n] = {};
+      if (gtile(kk) >= 0)
+        load_as<TG, TM, n>(reinterpret_cast<const TG *>(base + C::OFF_HG + gtile(kk) * C::HG_BYTES) +
+                               (ly + 2) * BXG + lx + HXG, gv);
 #pragma unroll
       for (int j = 0; j < n; ++j) {
-        pa[j] = fmaT(k.ag, g1[j], fmaT(k.aq, qv[j], pv[j]));
-        pb[j] = fmaT(k.bg, g2[j], fmaT(k.bq, qv[j], pv[j]));
+        TM v = pv[j];
+        if (uses_q(kk)) v = fmaT(k.kq[kk], qv[j], v);
+        if (gtile(kk) >= 0) v = fmaT(k.kg[kk], gv[j], v);
+        out[kk][j] = v;
       }
     }
   }
 
-  // x neighbours of both stage arguments for the lane's VEC points in row ly.
-  static __device__ __forceinline__ void xnb2(const unsigned char *base, const PairCoef<TM> &k,
-                                              int lane, int ly, const TM (&ca)[VEC],
-                                              const TM (&cb)[VEC], TM (&ea)[VEC + 4],
-                                              TM (&eb)[VEC + 4]) {
-    // e[i] = P at x - 2 + i, i = 0 .. VEC + 3
-    if constexpr (VEC >= 2) {
-      TM la0 = shfl_up1(ca[VEC - 2], 1), la1 = shfl_up1(ca[VEC - 1], 1);
-      TM lb0 = shfl_up1(cb[VEC - 2], 1), lb1 = shfl_up1(cb[VEC - 1], 1);
-      TM ra0 = shfl_dn1(ca[0], 1), ra1 = shfl_dn1(ca[1], 1);
-      TM rb0 = shfl_dn1(cb[0], 1), rb1 = shfl_dn1(cb[1], 1);
-      if (lane == 0) {
-        TM ha[2], hb[2];
-        comb2<2>(base, k, -2, ly, ha, hb);
-        la0 = ha[0]; la1 = ha[1]; lb0 = hb[0]; lb1 = hb[1];
-      } else if (lane == 31) {
-        TM ha[2], hb[2];
-        comb2<2>(base, k, TX, ly, ha, hb);
-        ra0 = ha[0]; ra1 = ha[1]; rb0 = hb[0]; rb1 = hb[1];
-      }
-      ea[0] = la0; ea[1] = la1; eb[0] = lb0; eb[1] = lb1;
+  // x neighbours e[kk][i] = P_kk at x - 2 + i (i = 0 .. VEC + 3) of the lane's
+  // points in row ly, given the own values c.
+  __device__ __forceinline__ void xnb(const unsigned char *base, int ly, const TM (&c)[KN][VEC],
+                                      TM (&e)[KN][VEC + 4]) const {
 #pragma unroll
-      for (int j = 0; j < VEC; ++j) { ea[2 + j] = ca[j]; eb[2 + j] = cb[j]; }
-      ea[VEC + 2] = ra0; ea[VEC + 3] = ra1; eb[VEC + 2] = rb0; eb[VEC + 3] = rb1;
-    } else {
-      TM ha[1] = {ca[0]}, hb[1] = {cb[0]};
-      if (lane < 2) comb2<1>(base, k, lane - 2, ly, ha, hb);
-      else if (lane >= 30) comb2<1>(base, k, TX + lane - 30, ly, ha, hb);
-      const TM a_u2 = shfl_up1(ca[0], 2), a_u1 = shfl_up1(ca[0], 1);
-      const TM a_d2 = shfl_dn1(ca[0], 2), a_d1 = shfl_dn1(ca[0], 1);
-      const TM b_u2 = shfl_up1(cb[0], 2), b_u1 = shfl_up1(cb[0], 1);
-      const TM b_d2 = shfl_dn1(cb[0], 2), b_d1 = shfl_dn1(cb[0], 1);
-      const TM a_h1 = shfl_idx(ha[0], 1), a_h30 = shfl_idx(ha[0], 30);
-      const TM b_h1 = shfl_idx(hb[0], 1), b_h30 = shfl_idx(hb[0], 30);
-      ea[0] = lane < 2 ? ha[0] : a_u2;
-      ea[1] = lane == 0 ? a_h1 : a_u1;
-      ea[2] = ca[0];
-      ea[3] = lane == 31 ? a_h30 : a_d1;
-      ea[4] = lane >= 30 ? ha[0] : a_d2;
-      eb[0] = lane < 2 ? hb[0] : b_u2;
-      eb[1] = lane == 0 ? b_h1 : b_u1;
-      eb[2] = cb[0];
-      eb[3] = lane == 31 ? b_h30 : b_d1;
-      eb[4] = lane >= 30 ? hb[0] : b_d2;
-    }
-  }
-
-  static __device__ __forceinline__ void run(const StageParams &prm, uint64_t *full,
-                                             uint64_t *empty, const unsigned char *ring,
-                                             volatile int *abort_flag, int warp, int lane) {
-    constexpr int RING = C::RING;
-    const int nitems = *prm.nitems;
-    const int lx0 = lane * VEC, ly0 = warp * VY;
-    int slot = 0;
-    uint32_t phase = 0;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-      const WorkItem w = prm.items[it];
-      Desc *d = prm.descs + w.x;
-      if (!item_active<S>(d, prm.k, warp == 0 && lane == 0)) continue;
-      const long long n = d->n_base + prm.k;
-      PairCoef<TM> k;
-      {
-        PairCoef<TM> c0;
-        if (lane == 0) c0 = pair_coef<C>(d, n);
-        const TM *src = reinterpret_cast<const TM *>(&c0);
-        TM *dst = reinterpret_cast<TM *>(&k);
+    for (int kk = 0; kk < KN; ++kk)
 #pragma unroll
-        for (int i = 0; i < (int)(sizeof(PairCoef<TM>) / sizeof(TM)); ++i)
-          dst[i] = shfl_idx(src[i], 0);
-      }
-      const int N = d->N;
-      const bool periodic = d->bc == 1;
-      const int set = (int)(n & 1);
-      const int so = set ^ 1;
-      const int x0 = (w.y & 0xffff) * TX, y0 = (w.y >> 16) * C::TY;
-      const int z0 = w.z, nplanes = w.w + 4;
-      const bool ragged = x0 + TX > N;
-      const int x = x0 + lx0;
-      const bool lane_edge = periodic && (x < 2 || x + VEC > N - 2);
-      const int64_t pitch_s = d->pitch_s, plane_s = d->plane_s;
-      const int64_t pitch_g = d->pitch_g, plane_g = d->plane_g;
-      const int64_t row_s = (int64_t)(y0 + ly0 + 2) * pitch_s + HXS + x;
-      const int64_t row_g = (int64_t)(y0 + ly0 + 2) * pitch_g + HXG + x;
-      const bool xok = x < N;
-      TG *outG1 = nullptr, *outG2 = nullptr;
-      TS *outP = nullptr, *outQ = nullptr, *outPL = nullptr, *outQL = nullptr;
-      if constexpr (S == 5) {
-        outG1 = reinterpret_cast<TG *>(d->f[F_G1]);
-        outG2 = reinterpret_cast<TG *>(d->f[F_G2]);
+      for (int j = 0; j < VEC; ++j) e[kk][2 + j] = c[kk][j];
+    if constexpr (S == 1) {
+      // P = p: neighbours straight from the halo tile
+      const TS *hp = reinterpret_cast<const TS *>(base) + (ly + 2) * BXS + lx0 + HXS;
+      if constexpr (VEC >= 2) {
+        TM a[2], b[2];
+        load_as<TS, TM, 2>(hp - 2, a);
+        load_as<TS, TM, 2>(hp + VEC, b);
+        e[0][0] = a[0]; e[0][1] = a[1]; e[0][VEC + 2] = b[0]; e[0][VEC + 3] = b[1];
       } else {
-        outP = reinterpret_cast<TS *>(d->f[F_P0 + so]);
-        outQ = reinterpret_cast<TS *>(d->f[F_Q0 + so]);
-        if constexpr (C::KAHAN) {
-          outPL = reinterpret_cast<TS *>(d->f[F_PLO0 + so]);
-          outQL = reinterpret_cast<TS *>(d->f[F_QLO0 + so]);
+        e[0][0] = (TM)hp[-2]; e[0][1] = (TM)hp[-1]; e[0][3] = (TM)hp[1]; e[0][4] = (TM)hp[2];
+      }
+    } else if constexpr (VEC >= 2) {
+      TM l0[KN], l1[KN], r0[KN], r1[KN];
+#pragma unroll
+      for (int kk = 0; kk < KN; ++kk) {
+        l0[kk] = shfl_up1(c[kk][VEC - 2], 1);
+        l1[kk] = shfl_up1(c[kk][VEC - 1], 1);
+        r0[kk] = shfl_dn1(c[kk][0], 1);
+        r1[kk] = shfl_dn1(c[kk][1], 1);
+      }
+      if (lane == 0 || lane == 31) {
+        TM h[KN][2];
+        comb<2>(base, lane == 0 ? -2 : TX, ly, h);
+#pragma unroll
+        for (int kk = 0; kk < KN; ++kk) {
+          if (lane == 0) { l0[kk] = h[kk][0]; l1[kk] = h[kk][1]; }
+          else { r0[kk] = h[kk][0]; r1[kk] = h[kk][1]; }
         }
       }
-      bool rok[VY];
 #pragma unroll
-      for (int r = 0; r < VY; ++r) rok[r] = xok && (y0 + ly0 + r < N);
+      for (int kk = 0; kk < KN; ++kk) {
+        e[kk][0] = l0[kk]; e[kk][1] = l1[kk]; e[kk][VEC + 2] = r0[kk]; e[kk][VEC + 3] = r1[kk];
+      }
+    } else {
+      TM h[KN][1];
+#pragma unroll
+      for (int kk = 0; kk < KN; ++kk) h[kk][0] = c[kk][0];
+      if (lane < 2 || lane >= 30) comb<1>(base, lane < 2 ? lane - 2 : TX + lane - 30, ly, h);
+#pragma unroll
+      for (int kk = 0; kk < KN; ++kk) {
+        const TM u2 = shfl_up1(c[kk][0], 2), u1 = shfl_up1(c[kk][0], 1);
+        const TM d2 = shfl_dn1(c[kk][0], 2), d1 = shfl_dn1(c[kk][0], 1);
+        const TM h1 = shfl_idx(h[kk][0], 1), h30 = shfl_idx(h[kk][0], 30);
+        e[kk][0] = lane < 2 ? h[kk][0] : u2;
+        e[kk][1] = lane == 0 ? h1 : u1;
+        e[kk][3] = lane == 31 ? h30 : d1;
+        e[kk][4] = lane >= 30 ? h[kk][0] : d2;
+      }
+    }
+  }
 
-      TM wa[5][VY][VEC], wb[5][VY][VEC];
-#pragma unroll
-      for (int a = 0; a < 5; ++a)
-#pragma unroll
-        for (int r = 0; r < VY; ++r)
-#pragma unroll
-          for (int j = 0; j < VEC; ++j) { wa[a][r][j] = (TM)0; wb[a][r][j] = (TM)0; }
-      TM run_max = (TM)0;
+  struct Item {
+    int N, x, z0, nplanes, set;
+    bool periodic, ragged, lane_edge, xok;
+    int64_t pitch_s, plane_s, pitch_g, plane_g, row_s, row_g;
+    int y0;
+    TG *outG0, *outG1;
+    TS *outP, *outQ, *outPL, *outQL;
+  };
 
-      for (int m = 0; m < nplanes; ++m) {
-        if (!mbar_wait_bounded(&full[slot], phase)) {
-          *abort_flag = 1;
-          atomicOr(prm.err, (unsigned)DEV_ERR_TIMEOUT);
-          return;
-        }
-        if (*abort_flag) return;
-        const unsigned char *base = ring + slot * C::SLOT_BYTES;
+  // One z-plane: plane m of the item enters the window (slot `slot`); for
+  // m >= 4 the output plane m - 4 (loaded as plane m - 2, slot s2) is computed.
+  // Window index of plane j is j mod 5, and m mod 5 == ROT.
+  template <int ROT>
+  __device__ __forceinline__ void plane(const Item &it, int m, int slot, int s2,
+                                        TM (&win)[5][KN][VY][VEC], TM &run_max,
+                                        bool &bad) const {
+    // ROT < 0: the window is shifted by one plane first and the newest plane
+    // lives at index 4; otherwise plane j lives at index j mod 5 (ROT = m mod 5).
+    constexpr int R0 = ROT < 0 ? 4 : ROT;
+    constexpr int W0 = R0 % 5, WM1 = (R0 + 4) % 5, WM2 = (R0 + 3) % 5, WM3 = (R0 + 2) % 5,
+                  WM4 = (R0 + 1) % 5;
+    if constexpr (ROT < 0) {
 #pragma unroll
-        for (int r = 0; r < VY; ++r) {
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) { wa[a][r][j] = wa[a + 1][r][j]; wb[a][r][j] = wb[a + 1][r][j]; }
-          comb2<VEC>(base, k, lx0, ly0 + r, wa[4][r], wb[4][r]);
-        }
-        const int s2 = slot >= 2 ? slot - 2 : slot + RING - 2;
-        if (m >= 4) {
-          const int z = z0 + m - 4;
-          const unsigned char *b2 = ring + s2 * C::SLOT_BYTES;
-          TM Ra[VY + 4][VEC], Rb[VY + 4][VEC];
-          comb2<VEC>(b2, k, lx0, ly0 - 2, Ra[0], Rb[0]);
-          comb2<VEC>(b2, k, lx0, ly0 - 1, Ra[1], Rb[1]);
-          comb2<VEC>(b2, k, lx0, ly0 + VY, Ra[VY + 2], Rb[VY + 2]);
-          comb2<VEC>(b2, k, lx0, ly0 + VY + 1, Ra[VY + 3], Rb[VY + 3]);
+        for (int kk = 0; kk < KN; ++kk)
 #pragma unroll
           for (int r = 0; r < VY; ++r)
 #pragma unroll
-            for (int j = 0; j < VEC; ++j) { Ra[r + 2][j] = wa[2][r][j]; Rb[r + 2][j] = wb[2][r][j]; }
+            for (int j = 0; j < VEC; ++j) win[a][kk][r][j] = win[a + 1][kk][r][j];
+    }
+    const unsigned char *base = ring + slot * C::SLOT_BYTES;
 #pragma unroll
-          for (int r = 0; r < VY; ++r) {
-            const int ly = ly0 + r;
-            const int y = y0 + ly;
-            TM ea[VEC + 4], eb[VEC + 4];
-            xnb2(b2, k, lane, ly, wa[2][r], wb[2][r], ea, eb);
-            const int hoff = (ly + 2) * BXS + lx0 + HXS;
-            TM qS[VEC];
-            load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(b2 + C::HS_BYTES) + hoff, qS);
-            TM Ga[VEC], Gb[VEC], g1[VEC], g2[VEC];
-            if constexpr (S == 6) {
-              const TG *hg = reinterpret_cast<const TG *>(b2 + C::OFF_HG) + (ly + 2) * BXG + lx0 + HXG;
-              load_as<TG, TM, VEC>(hg, g1);
-              load_as<TG, TM, VEC>(hg + C::HG_BYTES / (int)sizeof(TG), g2);
-            }
+    for (int r = 0; r < VY; ++r) {
+      TM t[KN][VEC];
+      comb<VEC>(base, lx0, ly0 + r, t);
 #pragma unroll
-            for (int j = 0; j < VEC; ++j) {
-              const TM Qa = (S == 6) ? fmaT(k.qa, g2[j], qS[j]) : qS[j];
-              Ga[j] = lap_g2(k.c43a, k.cm12a, k.ccena, k.nlam, k.m3, C::DIFF, wa[2][r][j], ea[j],
-                             ea[j + 1], ea[j + 3], ea[j + 4], Ra[r][j], Ra[r + 1][j], Ra[r + 3][j],
-                             Ra[r + 4][j], wa[0][r][j], wa[1][r][j], wa[3][r][j], wa[4][r][j], Qa);
-              const TM Qb = fmaT(k.qb, Ga[j], qS[j]);
-              Gb[j] = lap_g2(k.c43b, k.cm12b, k.ccenb, k.nlam, k.m3, C::DIFF, wb[2][r][j], eb[j],
-                             eb[j + 1], eb[j + 3], eb[j + 4], Rb[r][j], Rb[r + 1][j], Rb[r + 3][j],
-                             Rb[r + 4][j], wb[0][r][j], wb[1][r][j], wb[3][r][j], wb[4][r][j], Qb);
-            }
-            if (!rok[r]) continue;
-            const bool edge = lane_edge || (periodic && (y < 2 || y >= N - 2));
-            if constexpr (S == 5) {
-              const int64_t off = (int64_t)z * plane_g + row_g + r * pitch_g - x;
-              store_point<TG, TM, VEC>(outG1 + off, pitch_g, N, ragged, edge, x, y, Ga);
-              store_point<TG, TM, VEC>(outG2 + off, pitch_g, N, ragged, edge, x, y, Gb);
-            } else {
-              // RK4 combine (Sec. 2.1) with G3 = Ga, G4 = Gb
-              TM pS[VEC], lp[VEC], lq[VEC];
-              load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(b2) + hoff, pS);
-              if constexpr (C::KAHAN) {
-                const TS *is = reinterpret_cast<const TS *>(b2 + C::OFF_IS) + ly * TX + lx0;
-                load_as<TS, TM, VEC>(is, lp);
-                load_as<TS, TM, VEC>(is + C::IS_BYTES / (int)sizeof(TS), lq);
-              }
-              TM pn[VEC], qn[VEC], pl[VEC], ql[VEC];
+      for (int kk = 0; kk < KN; ++kk)
 #pragma unroll
-              for (int j = 0; j < VEC; ++j) {
-                const TM dp = fmaT(k.b6, (g1[j] + g2[j]) + Ga[j], k.dt * qS[j]);
-                const TM dq = k.d6 * ((g1[j] + Gb[j]) + (TM)2 * (g2[j] + Ga[j]));
-                if constexpr (C::KAHAN) {
-                  two_sum(pS[j], dp + lp[j], pn[j], pl[j]);
-                  two_sum(qS[j], dq + lq[j], qn[j], ql[j]);
-                } else {
-                  pn[j] = pS[j] + dp;
-                  qn[j] = qS[j] + dq;
-                }
-                if (x + j < N) {
-                  const TM av = pn[j] < (TM)0 ? -pn[j] : pn[j];
-                  run_max = (av <= run_max) ? run_max : ((av == av) ? av : (TM)INFINITY);
-                }
-              }
-              const int64_t off = (int64_t)z * plane_s + row_s + r * pitch_s - x;
-              store_point<TS, TM, VEC>(outP + off, pitch_s, N, ragged, edge, x, y, pn);
-              store_point<TS, TM, VEC>(outQ + off, pitch_s, N, ragged, edge, x, y, qn);
-              if constexpr (C::KAHAN) {
-                store_point<TS, TM, VEC>(outPL + off, pitch_s, N, ragged, edge, x, y, pl);
-                store_point<TS, TM, VEC>(outQL + off, pitch_s, N, ragged, edge, x, y, ql);
-              }
-            }
+        for (int j = 0; j < VEC; ++j) win[W0][kk][r][j] = t[kk][j];
+    }
+    if (m < 4) return;
+    // ---- output plane z = z0 + m - 4 (window: z-2 = W(m-4), z-1 = W(m-3),
+    // z = W(m-2), z+1 = W(m-1), z+2 = W(m))
+    const int z = it.z0 + m - 4;
+    const unsigned char *b2 = ring + s2 * C::SLOT_BYTES;
+    TM R[KN][4][VEC];  // rows ly0-2, ly0-1, ly0+VY, ly0+VY+1 of P at plane z
+    {
+      TM t[KN][VEC];
+      const int rows[4] = {ly0 - 2, ly0 - 1, ly0 + VY, ly0 + VY + 1};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        comb<VEC>(b2, lx0, rows[i], t);
+#pragma unroll
+        for (int kk = 0; kk < KN; ++kk)
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) R[kk][i][j] = t[kk][j];
+      }
+    }
+    // P of kind kk, row offset dy (in [-2, VY+1]) at plane z, lane point j
+    auto Pz = [&](int kk, int rr, int j) -> TM {
+      return rr < 0 ? R[kk][rr + 2][j] : (rr >= VY ? R[kk][rr - VY + 2][j] : win[WM2][kk][rr][j]);
+    };
+#pragma unroll
+    for (int r = 0; r < VY; ++r) {
+      const int ly = ly0 + r;
+      const int y = it.y0 + ly;
+      TM c[KN][VEC];
+#pragma unroll
+      for (int kk = 0; kk < KN; ++kk)
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) c[kk][j] = win[WM2][kk][r][j];
+      TM e[KN][VEC + 4];
+      xnb(b2, ly, c, e);
+      const int hoff = (ly + 2) * BXS + lx0 + HXS;
+      const int ioff = ly * TX + lx0;
+      // point-only values of plane z
+      TM qS[VEC], X[VEC] = {}, g1[VEC] = {}, g2[VEC] = {}, g3[VEC] = {}, lp[VEC] = {},
+                                lq[VEC] = {};
+      if constexpr (S == 1) {
+        load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(b2 + C::OFF_IS) + ioff, qS);
+      } else {
+        load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(b2 + C::HS_BYTES) + hoff, qS);
+      }
+      if constexpr (S == 2 || S == 3)  // G1 | G2 at the point
+        load_as<TG, TM, VEC>(reinterpret_cast<const TG *>(b2 + C::OFF_IG) + ioff, X);
+      if constexpr (S == 4) {
+        const TG *ig = reinterpret_cast<const TG *>(b2 + C::OFF_IG) + ioff;
+        load_as<TG, TM, VEC>(ig, g1);
+        load_as<TG, TM, VEC>(ig + C::IG_BYTES / (int)sizeof(TG), g3);
+        load_as<TG, TM, VEC>(reinterpret_cast<const TG *>(b2 + C::OFF_HG) + (ly + 2) * BXG + lx0 + HXG, g2);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) X[j] = g3[j];
+      }
+      if constexpr (S == 6) {
+        const TG *hg = reinterpret_cast<const TG *>(b2 + C::OFF_HG) + (ly + 2) * BXG + lx0 + HXG;
+        load_as<TG, TM, VEC>(hg, g1);
+        load_as<TG, TM, VEC>(hg + C::HG_BYTES / (int)sizeof(TG), g2);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) X[j] = g2[j];
+      }
+      if constexpr ((S == 4 || S == 6) && C::KAHAN) {
+        const TS *is = reinterpret_cast<const TS *>(b2 + C::OFF_IS) + ioff;
+        load_as<TS, TM, VEC>(is, lp);
+        load_as<TS, TM, VEC>(is + C::IS_BYTES / (int)sizeof(TS), lq);
+      }
+      TM res[KN][VEC];
+#pragma unroll
+      for (int kk = 0; kk < KN; ++kk) {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+          TM Q;
+          if (kk == 0) Q = (S == 1 || S == 5) ? qS[j] : fmaT(k.q0, X[j], qS[j]);
+          else Q = fmaT(k.q1, res[0][j], qS[j]);
+          res[kk][j] = lap_g(k.c43[kk], k.cm12[kk], k.ccen[kk], k.nlam, k.m3, C::DIFF, c[kk][j],
+                             e[kk][j], e[kk][j + 1], e[kk][j + 3], e[kk][j + 4], Pz(kk, r - 2, j),
+                             Pz(kk, r - 1, j), Pz(kk, r + 1, j), Pz(kk, r + 2, j),
+                             win[WM4][kk][r][j], win[WM3][kk][r][j], win[WM1][kk][r][j],
+                             win[W0][kk][r][j], Q);
+        }
+      }
+      const bool rok = it.xok && y < it.N;
+      const bool edge = it.lane_edge || (it.periodic && (y < 2 || y >= it.N - 2));
+      const bool fast = rok && !it.ragged && !edge;
+      if constexpr (S <= 3 || S == 5) {
+        const int64_t off = (int64_t)z * it.plane_g + it.row_g + r * it.pitch_g;
+        if (fast) {
+          store_as<TG, TM, VEC>(it.outG0 + off, res[0]);
+          if constexpr (S == 5) store_as<TG, TM, VEC>(it.outG1 + off, res[KN - 1]);
+        } else if (rok) {
+          store_point<TG, TM, VEC>(it.outG0 + off - it.x, it.pitch_g, it.N, it.ragged, edge, it.x, y, res[0]);
+          if constexpr (S == 5)
+            store_point<TG, TM, VEC>(it.outG1 + off - it.x, it.pitch_g, it.N, it.ragged, edge, it.x, y, res[KN - 1]);
+        }
+      } else {
+        // RK4 combine (Sec. 2.1): p' = p + dt q + dt^2/6 (G1 + G2 + G3),
+        //                         q' = q + dt/6 (G1 + 2 G2 + 2 G3 + G4)
+        if constexpr (S == 6) {
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) g3[j] = res[0][j];
+        }
+        const TM *G4 = res[KN - 1];
+        TM pS[VEC];
+        load_as<TS, TM, VEC>(reinterpret_cast<const TS *>(b2) + hoff, pS);
+        TM pn[VEC], qn[VEC], pl[VEC], ql[VEC];
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+          const TM dp = fmaT(k.b6, (g1[j] + g2[j]) + g3[j], k.dt * qS[j]);
+          const TM dq = k.d6 * ((g1[j] + G4[j]) + (TM)2 * (g2[j] + g3[j]));
+          if constexpr (C::KAHAN) {
+            two_sum(pS[j], dp + lp[j], pn[j], pl[j]);
+            two_sum(qS[j], dq + lq[j], qn[j], ql[j]);
+          } else {
+            pn[j] = pS[j] + dp;
+            qn[j] = qS[j] + dq;
+          }
+          // running max of |p'| over valid points; NaN and overflow read as +inf
+          TM av = pn[j] < (TM)0 ? -pn[j] : pn[j];
+          av = (av == av) ? av : (TM)INFINITY;
+          av = (rok && it.x + j < it.N) ? av : (TM)0;
+          run_max = av > run_max ? av : run_max;
+        }
+        const int64_t off = (int64_t)z * it.plane_s + it.row_s + r * it.pitch_s;
+        if (fast) {
+          store_as<TS, TM, VEC>(it.outP + off, pn);
+          store_as<TS, TM, VEC>(it.outQ + off, qn);
+          if constexpr (C::KAHAN) {
+            store_as<TS, TM, VEC>(it.outPL + off, pl);
+            store_as<TS, TM, VEC>(it.outQL + off, ql);
+          }
+        } else if (rok) {
+          store_point<TS, TM, VEC>(it.outP + off - it.x, it.pitch_s, it.N, it.ragged, edge, it.x, y, pn);
+          store_point<TS, TM, VEC>(it.outQ + off - it.x, it.pitch_s, it.N, it.ragged, edge, it.x, y, qn);
+          if constexpr (C::KAHAN) {
+            store_point<TS, TM, VEC>(it.outPL + off - it.x, it.pitch_s, it.N, it.ragged, edge, it.x, y, pl);
+            store_point<TS, TM, VEC>(it.outQL + off - it.x, it.pitch_s, it.N, it.ragged, edge, it.x, y, ql);
           }
         }
+      }
+    }
+    (void)bad;
+  }
+
+  static __device__ __forceinline__ void run(const StageParams &prm, uint64_t *full,
+                                             uint64_t *empty, const unsigned char *ring_,
+                                             volatile int *abort_flag, int warp, int lane_) {
+    Consumer self;
+    self.ring = ring_;
+    self.lane = lane_;
+    self.lx0 = lane_ * VEC;
+    self.ly0 = warp * VY;
+    const int nitems = *prm.nitems;
+    int slot = 0;
+    uint32_t phase = 0;
+    for (int itx = blockIdx.x; itx < nitems; itx += gridDim.x) {
+      const WorkItem w = prm.items[itx];
+      Desc *d = prm.descs + w.x;
+      if (!item_active<S>(d, prm.k, warp == 0 && lane_ == 0)) continue;
+      const long long n = d->n_base + prm.k;
+      {
+        UCoef<TM> c0;
+        if (lane_ == 0) c0 = unified_coef<C>(d, n);
+        const TM *src = reinterpret_cast<const TM *>(&c0);
+        TM *dst = reinterpret_cast<TM *>(&self.k);
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(UCoef<TM>) / sizeof(TM)); ++i) dst[i] = shfl_idx(src[i], 0);
+      }
+      Item it;
+      it.N = d->N;
+      it.periodic = d->bc == 1;
+      it.set = (int)(n & 1);
+      const int so = it.set ^ 1;
+      const int x0 = (w.y & 0xffff) * TX;
+      it.y0 = (w.y >> 16) * C::TY;
+      it.z0 = w.z;
+      it.nplanes = w.w + 4;
+      it.ragged = x0 + TX > it.N;
+      it.x = x0 + self.lx0;
+      it.xok = it.x < it.N;
+      // periodic ghost copies are written only by the lanes / rows next to a wrap
+      it.lane_edge = it.periodic && (it.x < 2 || it.x + VEC > it.N - 2);
+      it.pitch_s = d->pitch_s; it.plane_s = d->plane_s;
+      it.pitch_g = d->pitch_g; it.plane_g = d->plane_g;
+      it.row_s = (int64_t)(it.y0 + self.ly0 + 2) * it.pitch_s + HXS + it.x;
+      it.row_g = (int64_t)(it.y0 + self.ly0 + 2) * it.pitch_g + HXG + it.x;
+      it.outG0 = it.outG1 = nullptr;
+      it.outP = it.outQ = it.outPL = it.outQL = nullptr;
+      if constexpr (S <= 3) it.outG0 = reinterpret_cast<TG *>(d->f[S == 1 ? F_G1 : (S == 2 ? F_G2 : F_G3)]);
+      if constexpr (S == 5) {
+        it.outG0 = reinterpret_cast<TG *>(d->f[F_G1]);
+        it.outG1 = reinterpret_cast<TG *>(d->f[F_G2]);
+      }
+      if constexpr (S == 4 || S == 6) {
+        it.outP = reinterpret_cast<TS *>(d->f[F_P0 + so]);
+        it.outQ = reinterpret_cast<TS *>(d->f[F_Q0 + so]);
+        if constexpr (C::KAHAN) {
+          it.outPL = reinterpret_cast<TS *>(d->f[F_PLO0 + so]);
+          it.outQL = reinterpret_cast<TS *>(d->f[F_QLO0 + so]);
+        }
+      }
+      TM win[5][KN][VY][VEC];
+#pragma unroll
+      for (int a = 0; a < 5; ++a)
+#pragma unroll
+        for (int kk = 0; kk < KN; ++kk)
+#pragma unroll
+          for (int r = 0; r < VY; ++r)
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) win[a][kk][r][j] = (TM)0;
+      TM run_max = (TM)0;
+      bool bad = false;
+      // one plane: wait for its slot, compute, release what is no longer needed
+      auto step = [&](auto rot, int m) -> bool {
+        if (!mbar_wait_bounded(&full[slot], phase)) {
+          *abort_flag = 1;
+          atomicOr(prm.err, (unsigned)DEV_ERR_TIMEOUT);
+          return false;
+        }
+        if (*abort_flag) return false;
+        const int s2 = slot >= 2 ? slot - 2 : slot + RING - 2;  // slot of plane m - 2
+        self.template plane<decltype(rot)::value>(it, m, slot, s2, win, run_max, bad);
         __syncwarp();
-        if (lane == 0) {
-          if (m < 2 || m >= nplanes - 2) mbar_arrive(&empty[slot]);
+        if (self.lane == 0) {
+          if (m < 2 || m >= it.nplanes - 2) mbar_arrive(&empty[slot]);
           if (m >= 4) mbar_arrive(&empty[s2]);
         }
         if (++slot == RING) { slot = 0; phase ^= 1u; }
-      }
-      if constexpr (S == 6) {
+        return true;
+      };
+      bool ok = true;
+      for (int m = 0; ok && m < it.nplanes; ++m) ok = step(std::integral_constant<int, -1>{}, m);
+      if (!ok) return;
+      if constexpr (S == 4 || S == 6) {
         double v = (double)run_max;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (lane == 0) atomicMax(d->maxabs + prm.k, (unsigned long long)__double_as_longlong(v));
+        if (lane_ == 0) atomicMax(d->maxabs + prm.k, (unsigned long long)__double_as_longlong(v));
       }
     }
   }
@@ -1047,8 +837,6 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
   __syncthreads();
   if (warp == C::NW) {
     if (lane == 0) produce<C>(prm, full, empty, ring, abort_flag);
-  } else if constexpr (C::PAIR) {
-    PairConsumer<C>::run(prm, full, empty, ring, abort_flag, warp, lane);
   } else {
     Consumer<C>::run(prm, full, empty, ring, abort_flag, warp, lane);
   }

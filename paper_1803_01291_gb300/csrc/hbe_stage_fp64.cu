@@ -28,8 +28,7 @@ const VariantTable &variants_fp64() {
     // <precision, x points per lane, rows per warp, consumer warps, smem budget, min blocks/SM>
     add<PR, 1, 2, 8, 110 * 1024, 1>(t);  // 32 x 16 tile, 9 warps
     add<PR, 2, 1, 8, 110 * 1024, 1>(t);  // 64 x 8 tile, 9 warps
-    add<PR, 2, 2, 4, 110 * 1024, 1>(t);  // 64 x 8 tile, 5 warps
-    add<PR, 2, 2, 8, 220 * 1024, 1>(t);  // 64 x 16 tile, 9 warps
+    add<PR, 2, 1, 4, 110 * 1024, 1>(t);  // 64 x 4 tile, 5 warps
     return t;
   }();
   return table;

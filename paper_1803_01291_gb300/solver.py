@@ -113,6 +113,10 @@ class Solver:
     def set_tuning(self, variant: int, zchunk: int = 0):
         self._chk(self.lib.hbe_set_tuning(self._ctx, variant, zchunk))
 
+    def set_schedule(self, schedule: int):
+        """0: four one-stage kernels per RK4 step; 1 (default): two fused pairs."""
+        self._chk(self.lib.hbe_set_schedule(self._ctx, schedule))
+
     def set_stop(self, threshold: float):
         self._chk(self.lib.hbe_set_stop(self._ctx, threshold))
 
@@ -210,6 +214,13 @@ class Solver:
         if masks:
             d["pos_mask"], d["neg_mask"] = pm, nm
         return d
+
+    def analysis(self, eps: float = 0.0) -> dict:
+        """Sec. 3 analysis quantities: integral of phi and phi^3, the Laplacian
+        monitor e^{-2t} max|Lap phi|, and the first bubble condition's violations."""
+        out = _lib.HbeAnalysis()
+        self._chk(self.lib.hbe_analysis(self._ctx, eps, ctypes.byref(out)))
+        return {f: getattr(out, f) for f, _ in _lib.HbeAnalysis._fields_}
 
     def save(self, path: str):
         self._chk(self.lib.hbe_save(self._ctx, path.encode()))

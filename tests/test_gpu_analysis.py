@@ -1,0 +1,61 @@
+"""The Sec. 3 analysis quantities computed on the device (hbe_analysis) against
+their definitions evaluated on the same field on the host: h^3 sum phi,
+h^3 sum phi^3, e^{-2t} max |FD4 Laplacian| (the oracle's Laplacian), and the
+first bubble condition of the corollary quoted in Example 3."""
+import math
+
+import numpy as np
+import pytest
+
+import __graft_entry__  # noqa: F401
+import hbe_inputs as hi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hbe():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1803_01291_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_analysis_matches_definitions(hbe, prec, bc):
+    N, L, mu, lam = 36, 10.0, 3.0, 2.0
+    rng = np.random.default_rng(bc)
+    from scipy import ndimage
+    mode = "wrap" if bc == 1 else "constant"
+    phi0 = ndimage.gaussian_filter(rng.standard_normal((N, N, N)), 2.0, mode=mode) * 3
+    phi1 = -5 * phi0 + 0.1 * ndimage.gaussian_filter(rng.standard_normal((N, N, N)), 2.0, mode=mode)
+    h = hi.grid_spacing(N, L, bc)
+    with hbe.Solver(N, L, mu, lam, bc, prec) as s:
+        s.set_initial(phi0, phi1)
+        s.step(5, h / 4)
+        phi, psi, t = s.read()
+        a = s.analysis(eps=1e-3)
+    assert a["t"] == t
+    assert math.isclose(a["integral_phi"], h ** 3 * math.fsum(phi.ravel()), rel_tol=1e-12, abs_tol=1e-12)
+    assert math.isclose(a["integral_phi3"], h ** 3 * math.fsum((phi ** 3).ravel()), rel_tol=1e-12, abs_tol=1e-12)
+    lap = oracle.laplacian(phi, h, bc)
+    assert math.isclose(a["laplacian_monitor"], math.exp(-2 * t) * np.max(np.abs(lap)), rel_tol=1e-12)
+    m = 1.5 + math.sqrt(2.25 + mu * mu)
+    support = np.abs(phi) + np.abs(psi) > 1e-3
+    assert a["support_points"] == int(support.sum())
+    assert a["condition1_violations"] == int((support & (m * phi + psi >= 0)).sum())
+
+
+def test_homogeneous_integral_is_volume_times_value(hbe):
+    N, L = 16, 4.0
+    with hbe.Solver(N, L, 1.0, 1.0, 1, 0) as s:
+        s.set_initial(np.full((N, N, N), 0.7), np.zeros((N, N, N)))
+        a = s.analysis()
+    assert math.isclose(a["integral_phi"], 0.7 * L ** 3, rel_tol=1e-14)
+    assert math.isclose(a["integral_phi3"], 0.7 ** 3 * L ** 3, rel_tol=1e-14)
+    # the FD4 weights sum to zero; on a constant only rounding of the weighted
+    # terms (a few ulp of 15/h^2 * 0.7) is left
+    assert a["laplacian_monitor"] <= 1e-13

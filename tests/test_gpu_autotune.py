@@ -26,12 +26,12 @@ def test_tune_caches_and_applies(hbe, tmp_path, monkeypatch):
     N = 48
     entry = autotune.tune(N, 0, hbe.FP32, steps=3)
     nvar = len(hbe.variants(hbe.FP32))
-    assert len(entry["sweep"]) == nvar * len(list(autotune.zchunk_candidates(N)))
-    best = min(entry["sweep"], key=lambda r: r[2])
-    assert (entry["variant"], entry["zchunk"]) == (best[0], best[1])
+    assert len(entry["sweep"]) == 2 * nvar * len(list(autotune.zchunk_candidates(N)))
+    best = min(entry["sweep"], key=lambda r: r[3])
+    assert (entry["variant"], entry["zchunk"], entry["schedule"]) == tuple(best[:3])
     cache = json.load(open(tmp_path / "cache.json"))
     assert len(cache) == 1
-    assert autotune.best(N, 0, hbe.FP32) == (entry["variant"], entry["zchunk"])
+    assert autotune.best(N, 0, hbe.FP32) == (entry["variant"], entry["zchunk"], entry["schedule"])
     rng = np.random.default_rng(1)
     phi0 = rng.standard_normal((N, N, N)) * 0.1
     out = []
