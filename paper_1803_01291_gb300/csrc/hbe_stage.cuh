@@ -108,6 +108,7 @@ struct StageCfg {
   static constexpr int HEADER = 384;  // 2 x 16 mbarriers, flags
   static constexpr int RING = cmax(4, cmin(16, (BUDGET_ - HEADER) / SLOT_BYTES));
   static constexpr int SMEM = HEADER + RING * SLOT_BYTES;
+  static_assert(SMEM <= 227 * 1024, "ring of 4 slots does not fit in 227 KB of shared memory");
   static constexpr int MINB = MINB_;  // blocks per SM the registers must allow
   static_assert(VEC == 1 || VEC == 2 || VEC == 4, "1, 2 or 4 x points per lane");
   static_assert(VEC * (int)sizeof(TM) <= 16, "lane vector of <= 16 bytes");
