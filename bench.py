@@ -71,9 +71,10 @@ def measured_peaks():
 FP64_FMA_PER_S = 0.58e12
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(prec: str = "fp32") -> str:
+    """Hash of the stage-kernel sources and the precision's tile-variant table."""
     h = hashlib.sha256()
-    for fn in ("hbe_stage.cuh", "hbe_common.cuh"):
+    for fn in ("hbe_stage.cuh", "hbe_common.cuh", f"hbe_stage_{prec}.cu"):
         with open(os.path.join(ROOT, "paper_1803_01291_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -101,7 +102,7 @@ def recorded_traffic(prec: str, N: int, schedule: int = 1):
         if "=" in line and not line.startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+    if kv.get("kernel_source_sha256_16") != kernel_source_hash(prec):
         return None
     try:
         per_point = float(kv["dram_bytes_per_point"])
