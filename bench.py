@@ -246,16 +246,19 @@ def e2e_solve(hbe, torch, prob, prec_id, nsteps):
     s.set_initial(h0.numpy(), h1.numpy())
     s.step(2, prob.dt)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    s.set_initial(h0.numpy(), h1.numpy())
-    st = s.step(nsteps, prob.dt)
     import ctypes
     tt = ctypes.c_double()
     dp = ctypes.POINTER(ctypes.c_double)
+    t0 = time.perf_counter()
+    s.set_initial(h0.numpy(), h1.numpy())
+    t1 = time.perf_counter()
+    st = s.step(nsteps, prob.dt)
+    t2 = time.perf_counter()
     s.lib.hbe_read(s.handle, ctypes.cast(out.data_ptr(), dp), None, ctypes.byref(tt))
-    secs = time.perf_counter() - t0
+    t3 = time.perf_counter()
     s.close()
-    return secs, st, float(np.abs(out.numpy()).max())
+    phases = {"initial_data_s": t1 - t0, "steps_s": t2 - t1, "read_s": t3 - t2}
+    return t3 - t0, st, float(np.abs(out.numpy()).max()), phases
 
 
 def serve_leg(hbe, count: int = 256, seed: int = 0, load: float = 0.8):
@@ -465,13 +468,14 @@ def main():
 
     if not args.no_e2e:
         nsteps = 308 if N == 512 else max(8, int(round(HORIZON / prob.dt)))
-        e2e_secs, st, _ = e2e_solve(hbe, torch, prob, hbe.FP32, nsteps)
+        e2e_secs, st, _, phases = e2e_solve(hbe, torch, prob, hbe.FP32, nsteps)
         e2e_secs = max_over_ranks(e2e_secs, world, torch, device)
         line["e2e"] = {"value": float(N) ** 3 * nsteps * world / e2e_secs / 1e9,
                        "unit": "Gpoint-steps/s",
                        "h2d_bytes_per_step": 2 * 8 * N ** 3 / nsteps,
                        "d2h_bytes_per_step": 8 * N ** 3 / nsteps,
                        "steps_per_solve": nsteps,
+                       "phases": phases,
                        "note": "one solve: phi0, phi1 from pinned host, nsteps RK4 steps, phi to "
                                "pinned host; bytes amortised per RK4 step"}
 

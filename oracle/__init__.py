@@ -7,7 +7,9 @@ imports it and has no CPU fallback.
 `hbe_oracle.c` is the plain FP64 restatement of Sec. 2.1 of the paper (FD4
 Laplacian, Eq. (rhs), textbook RK4); this module compiles it with gcc on first
 use and wraps it with ctypes.  `radial.py` holds the 1D u = r*phi solver used as
-an independent pin.
+an independent pin; `radial_phi.py` is the paper's own radial scheme (Sec. 2.2,
+phi form with the L'Hospital closure at the origin), the oracle of the batched
+radial GPU solver.
 
 Parity: every function here is pinned by tests/test_oracle_pins.py against
 closed forms, library ODE solvers, invariants or brute force.

@@ -75,8 +75,10 @@ struct hbe_ctx {
   unsigned *d_err = nullptr;
   int K = 8;
   cudaGraphExec_t gexec = nullptr;
-  double *d_stage = nullptr;
+  double *d_stage = nullptr;   // 2 buffer sets x 2 fields x stage_elems doubles
   size_t stage_elems = 0;
+  cudaStream_t copy_stream = nullptr;   // host <-> staging copies
+  cudaEvent_t ev_ready[2] = {}, ev_free[2] = {};
   uint32_t *d_masks = nullptr;
   int *d_labels = nullptr;
   unsigned long long *d_counts = nullptr;
@@ -304,10 +306,15 @@ hbe_status ensure_graph(hbe_ctx *ctx) {
 hbe_status ensure_stage_buffer(hbe_ctx *ctx) {
   if (ctx->d_stage) return HBE_OK;
   const size_t plane = (size_t)ctx->N * ctx->N;
-  size_t planes = std::max<size_t>(1, (size_t)(8u << 20) / plane);  // <= 64 MiB of doubles
+  size_t planes = std::max<size_t>(1, (size_t)(4u << 20) / plane);  // <= 32 MiB of doubles
   planes = std::min<size_t>(planes, (size_t)ctx->N);
+  if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  for (int b = 0; b < 2; ++b) {
+    if (!ctx->ev_ready[b]) CK(cudaEventCreateWithFlags(&ctx->ev_ready[b], cudaEventDisableTiming));
+    if (!ctx->ev_free[b]) CK(cudaEventCreateWithFlags(&ctx->ev_free[b], cudaEventDisableTiming));
+  }
+  CK(cudaMalloc(&ctx->d_stage, 4 * planes * plane * sizeof(double)));
   ctx->stage_elems = planes * plane;
-  CK(cudaMalloc(&ctx->d_stage, 2 * ctx->stage_elems * sizeof(double)));
   return HBE_OK;
 }
 
@@ -498,6 +505,11 @@ void hbe_destroy(hbe_ctx *ctx) {
   cudaFree(ctx->d_one);
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_stage);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  for (int b = 0; b < 2; ++b) {
+    if (ctx->ev_ready[b]) cudaEventDestroy(ctx->ev_ready[b]);
+    if (ctx->ev_free[b]) cudaEventDestroy(ctx->ev_free[b]);
+  }
   cudaFree(ctx->d_masks);
   cudaFree(ctx->d_labels);
   cudaFree(ctx->d_counts);
@@ -582,22 +594,28 @@ static hbe_status set_initial_impl(hbe_ctx *ctx, const double *phi0, const doubl
     CK(launch_pack(sprec, phi1, ctx->f[F_Q0], kahan ? ctx->f[F_QLO0] : nullptr, N, ctx->pitch_s,
                    ctx->hxs, ctx->bc, 0, N, ctx->stream));
   } else {
+    // chunks of planes through two staging sets: the copy of chunk i + 1
+    // (copy stream) overlaps the pack of chunk i (work stream)
     if ((st = ensure_stage_buffer(ctx)) != HBE_OK) return st;
     const int zs = (int)(ctx->stage_elems / plane);
-    double *s0 = ctx->d_stage, *s1 = ctx->d_stage + ctx->stage_elems;
-    for (int z = 0; z < N; z += zs) {
-      const int nz = std::min(zs, N - z);
+    for (int z = 0, i = 0; z < N; z += zs, ++i) {
+      const int nz = std::min(zs, N - z), b = i & 1;
+      double *s0 = ctx->d_stage + 2 * b * ctx->stage_elems, *s1 = s0 + ctx->stage_elems;
+      if (i >= 2) CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[b], 0));
       CK(cudaMemcpyAsync(s0, phi0 + (size_t)z * plane, nz * plane * sizeof(double),
-                         cudaMemcpyHostToDevice, ctx->stream));
+                         cudaMemcpyHostToDevice, ctx->copy_stream));
       CK(cudaMemcpyAsync(s1, phi1 + (size_t)z * plane, nz * plane * sizeof(double),
-                         cudaMemcpyHostToDevice, ctx->stream));
+                         cudaMemcpyHostToDevice, ctx->copy_stream));
+      CK(cudaEventRecord(ctx->ev_ready[b], ctx->copy_stream));
+      CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_ready[b], 0));
       CK(launch_pack(sprec, s0, ctx->f[F_P0],
                      kahan ? ctx->f[F_PLO0] : nullptr, N, ctx->pitch_s, ctx->hxs, ctx->bc, z, nz,
                      ctx->stream));
       CK(launch_pack(sprec, s1, ctx->f[F_Q0], kahan ? ctx->f[F_QLO0] : nullptr, N, ctx->pitch_s,
                      ctx->hxs, ctx->bc, z, nz, ctx->stream));
-      CK(cudaStreamSynchronize(ctx->stream));
+      CK(cudaEventRecord(ctx->ev_free[b], ctx->stream));
     }
+    CK(cudaStreamSynchronize(ctx->stream));
   }
   Desc &d = *ctx->h_desc;
   d.t0 = t0;
@@ -817,25 +835,29 @@ static hbe_status read_impl(hbe_ctx *ctx, double *phi, double *psi, bool device)
     if (psi) CK(launch_unpack(sprec, hq, lq, psi, N, ctx->pitch_s, ctx->hxs, 0, N, ctx->stream));
     return HBE_OK;
   }
+  // chunks of planes through two staging sets: the unpack of chunk i + 1
+  // (work stream) overlaps the copy of chunk i to the host (copy stream)
   hbe_status st = ensure_stage_buffer(ctx);
   if (st != HBE_OK) return st;
   const size_t plane = (size_t)N * N;
   const int zs = (int)(ctx->stage_elems / plane);
-  for (int z = 0; z < N; z += zs) {
-    const int nz = std::min(zs, N - z);
-    if (phi) {
-      CK(launch_unpack(sprec, hp, lp, ctx->d_stage, N, ctx->pitch_s, ctx->hxs, z, nz, ctx->stream));
-      CK(cudaMemcpyAsync(phi + (size_t)z * plane, ctx->d_stage, nz * plane * sizeof(double),
-                         cudaMemcpyDeviceToHost, ctx->stream));
-    }
-    if (psi) {
-      CK(launch_unpack(sprec, hq, lq, ctx->d_stage + ctx->stage_elems, N, ctx->pitch_s, ctx->hxs, z,
-                       nz, ctx->stream));
-      CK(cudaMemcpyAsync(psi + (size_t)z * plane, ctx->d_stage + ctx->stage_elems,
-                         nz * plane * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    }
-    CK(cudaStreamSynchronize(ctx->stream));
+  for (int z = 0, i = 0; z < N; z += zs, ++i) {
+    const int nz = std::min(zs, N - z), b = i & 1;
+    double *s0 = ctx->d_stage + 2 * b * ctx->stage_elems, *s1 = s0 + ctx->stage_elems;
+    if (i >= 2) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_free[b], 0));
+    if (phi) CK(launch_unpack(sprec, hp, lp, s0, N, ctx->pitch_s, ctx->hxs, z, nz, ctx->stream));
+    if (psi) CK(launch_unpack(sprec, hq, lq, s1, N, ctx->pitch_s, ctx->hxs, z, nz, ctx->stream));
+    CK(cudaEventRecord(ctx->ev_ready[b], ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_ready[b], 0));
+    if (phi)
+      CK(cudaMemcpyAsync(phi + (size_t)z * plane, s0, nz * plane * sizeof(double),
+                         cudaMemcpyDeviceToHost, ctx->copy_stream));
+    if (psi)
+      CK(cudaMemcpyAsync(psi + (size_t)z * plane, s1, nz * plane * sizeof(double),
+                         cudaMemcpyDeviceToHost, ctx->copy_stream));
+    CK(cudaEventRecord(ctx->ev_free[b], ctx->copy_stream));
   }
+  CK(cudaStreamSynchronize(ctx->copy_stream));
   return HBE_OK;
 }
 

@@ -18,6 +18,7 @@ from scipy.special import jv, yv
 import hbe_inputs as hi
 import oracle
 from oracle import radial
+from oracle import radial_phi
 
 D, P = oracle.DIRICHLET, oracle.PERIODIC
 
@@ -473,6 +474,82 @@ def test_window_values_equal_full_grid_values(bc):
     w = oracle.window_values(phi0, phi1, L, 1.0, 1.0, bc, 0.3, dt, nsteps, pts)
     for i, pt in enumerate(pts):
         assert w[i, 0] == pf[pt] and w[i, 1] == qf[pt]
+
+
+# ---------------------------------------------------------------- P11 radial phi form (Sec. 2.2)
+def test_radial_phi_operator_exact_on_even_polynomials():
+    """phi_rr + (2/r) phi_r of r^2 is 6 and of r^4 is 20 r^2, at the origin
+    too (3 phi_rr(0) with the even closure); FD4 and the even ghosts are exact
+    on these, so only rounding remains away from the two wall nodes."""
+    n, R = 40, 4.0
+    dr = R / n
+    r = np.arange(n) * dr
+    inner = slice(0, n - 2)
+    l2 = radial_phi.laplacian(r ** 2, dr)
+    l4 = radial_phi.laplacian(r ** 4, dr)
+    assert np.max(np.abs(l2[inner] - 6.0)) < 1e-10
+    assert np.max(np.abs(l4[inner] - 20.0 * r[inner] ** 2)) < 1e-9
+    assert abs(l2[0] - 6.0) < 1e-12 and abs(l4[0]) < 1e-12
+
+
+def test_radial_phi_spherical_mode_matches_ode_at_fourth_order():
+    """lambda = 0: phi = a(t) sin(kr)/(kr) with k = 3 pi / R (zero at the wall)
+    solves Eq. (radial) when a'' + 3a' + (e^{-2t} k^2 - mu^2) a = 0 (DOP853).
+    Away from the wall (where the zero ghosts act) the grid error falls 16x per
+    halving of dr."""
+    R, mu, T = 10.0, 1.0, 1.0
+    k = 3 * math.pi / R
+    sol = solve_ivp(lambda t, y: [y[1], -3 * y[1] - (math.exp(-2 * t) * k * k - mu * mu) * y[0]],
+                    (0, T), [1.0, 0.0], method="DOP853", rtol=1e-13, atol=1e-15)
+    a = sol.y[0, -1]
+    errs = []
+    for n in (100, 200, 400):
+        dr = R / n
+        r = np.arange(n) * dr
+        phi0 = np.sinc(k * r / math.pi)
+        nst = int(round(T / (dr / 4)))
+        out = radial_phi.run(phi0, 0 * phi0, R, mu, 0.0, 0.0, T / nst, nst)
+        sel = r <= R - 2
+        errs.append(np.max(np.abs(out["phi"][sel] - a * phi0[sel])))
+    assert errs[-1] < 1e-9
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 3.8 <= math.log2(e1 / e2) <= 4.2
+
+
+def test_radial_phi_agrees_with_u_form_solver():
+    """The paper's phi form and the u = r phi form are different
+    discretisations of the same problem: on a bump (mu = lambda = 1, t = 1)
+    they agree to O(dr^4), including the origin value."""
+    def f0(r):
+        return np.where(r < 3, 1.5 * np.exp(-1.0 / np.maximum(1 - r * r / 9.0, 1e-300)), 0.0)
+
+    ru, pu = radial.solve(f0, lambda r: 0 * r, 8.0, 4000, 1.0, 1.0, 1.0, 8.0 / 4000 / 4)
+    ref = CubicSpline(ru, pu)
+    errs = []
+    for n in (200, 400):
+        dr = 8.0 / n
+        r = np.arange(n) * dr
+        nst = int(round(1.0 / (dr / 4)))
+        out = radial_phi.run(f0(r), 0 * r, 8.0, 1.0, 1.0, 0.0, 1.0 / nst, nst)
+        sel = (r > 0) & (r < 6)
+        errs.append(np.max(np.abs(out["phi"][sel] - ref(r[sel]))))
+        assert abs(out["phi"][0] - ref(0.0)) < 1e-8
+    assert errs[1] < 1e-6 and errs[0] / errs[1] > 10
+
+
+def test_radial_phi_sign_changes_and_stop_rule():
+    assert radial_phi.sign_changes(np.array([1.0, 0.5, -0.2, 0.0, -1e-9, 0.3]), 1e-6) == 2
+    assert radial_phi.sign_changes(np.array([0.0, 0.0]), 0.0) == 0
+    assert radial_phi.sign_changes(np.array([-1.0, -2.0, 3.0]), 0.0) == 1
+    # focusing data: the run ends after the first step above the threshold
+    n, R = 100, 10.0
+    r = np.arange(n) * R / n
+    phi0 = 3.0 * np.exp(-r * r)
+    out = radial_phi.run(phi0, 0 * r, R, 1.0, -1.0, 0.0, 0.025, 400, stop=1e3)
+    assert out["status"] == 1 and out["steps"] < 400
+    assert np.max(np.abs(out["phi"])) > 1e3
+    prev = radial_phi.run(phi0, 0 * r, R, 1.0, -1.0, 0.0, 0.025, out["steps"] - 1)
+    assert np.max(np.abs(prev["phi"])) <= 1e3
 
 
 # ---------------------------------------------------------------- input generators
