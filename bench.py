@@ -308,6 +308,85 @@ def cpu_baseline(prob, nsteps=2):
                       f"OpenMP over z, {cores} threads), {secs:.2f} s"}
 
 
+# floating-point operations of one radial node-step (four stages of the Laplacian
+# with its 2/r term, 14; the right-hand side, 9; the stage arguments and the RK4
+# combine), counted with an FMA as two
+RADIAL_FLOPS_PER_NODE_STEP = 121
+# FP32 lanes: 152 SMs x 128 lanes x 2 flops (FMA) x 2.07 GHz
+FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9
+
+
+def radial_workload(batch: int = 1216, n: int = 2000, seed: int = 0):
+    """A seeded parameter sweep of radial problems in the paper's units (Sec. 3:
+    L = 5, the bump B(r; 0, R0), mu^2 in [0.1, 9], lambda in [0.1, 2]): phi0 =
+    A B(r; 0, R0) with A in [0.5, 3], R0 in [0.1, 0.4] (unit box), phi1 = kappa
+    phi0 with kappa in [-5, 5]; n nodes on [0, 5], dt = 1e-3, 2000 steps."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    R = 5.0
+    r = np.arange(n) * R / n / R  # unit-box radius
+    A = rng.uniform(0.5, 3.0, batch)
+    R0 = rng.uniform(0.1, 0.4, batch)
+    kap = rng.uniform(-5.0, 5.0, batch)
+    mu = np.sqrt(rng.uniform(0.1, 9.0, batch))
+    lam = rng.uniform(0.1, 2.0, batch)
+    s = (r[None, :] / R0[:, None]) ** 2
+    inside = s < 1
+    B = np.zeros((batch, n))
+    B[inside] = np.exp((1.0 / R0[:, None] ** 2 - 1.0 / (R0[:, None] ** 2 - r[None, :] ** 2))[inside])
+    phi0 = A[:, None] * B
+    phi1 = kap[:, None] * phi0
+    dt = R / n / 4
+    return {"R": R, "n": n, "dt": dt, "nsteps": int(round(2.0 / dt)), "phi0": phi0, "phi1": phi1,
+            "mu": mu, "lam": lam}
+
+
+def radial_leg(hbe, torch, cpu: bool = True):
+    """Batched radial solver (Sec. 2.2) on the sweep above, FP32 and FP64:
+    node-steps per second over one launch that integrates every problem, timed
+    with CUDA events; the FP32 roofline is the FP32 FMA rate of the SMs, the
+    FP64 one the measured FP64 FMA rate.  CPU: the radial oracle (FP64 numpy)
+    on one problem for 2000 steps."""
+    from paper_1803_01291_gb300 import radial
+    w = radial_workload()
+    B, n = w["phi0"].shape
+    phi0 = torch.from_numpy(w["phi0"]).cuda()
+    phi1 = torch.from_numpy(w["phi1"]).cuda()
+    out = {"workload": f"{B} radial problems, n = {n} nodes on [0, 5], dt = {w['dt']:g}, "
+                       f"{w['nsteps']} steps, records every 100 steps, stop at 1e6 (seed 0)"}
+    for name, prec, peak in (("fp32", hbe.FP32, FP32_PEAK_FLOPS),
+                             ("fp64", hbe.FP64, 2 * FP64_FMA_PER_S)):
+        radial.run(phi0, phi1, w["R"], w["mu"], w["lam"], 0.0, w["dt"], 20, prec=prec)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        res = radial.run(phi0, phi1, w["R"], w["mu"], w["lam"], 0.0, w["dt"], w["nsteps"],
+                         prec=prec, record_every=100, stop=1e6)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        node_steps = float(res.steps.sum().item()) * n
+        rate = node_steps / secs
+        out[name] = {"value": rate / 1e9, "unit": "Gnode-steps/s", "seconds": secs,
+                     "stopped": int((res.status.cpu() != 0).sum().item()),
+                     "roofline": {"bound": "alu", "achieved": rate * RADIAL_FLOPS_PER_NODE_STEP / 1e12,
+                                  "peak": peak / 1e12, "unit": "TFLOP/s",
+                                  "frac": rate * RADIAL_FLOPS_PER_NODE_STEP / peak,
+                                  "peak_kind": "nominal FP32 FMA rate (152 SMs x 128 lanes x 2.07 GHz)"
+                                  if prec == hbe.FP32 else "measured FP64 FMA rate"}}
+    if cpu:
+        import oracle.radial_phi as rp
+        t0 = time.perf_counter()
+        rp.run(w["phi0"][0], w["phi1"][0], w["R"], w["mu"][0], w["lam"][0], 0.0, w["dt"], 2000)
+        secs = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": n * 2000 / secs / 1e9, "unit": "Gnode-steps/s",
+                               "cores": 1, "kind": "oracle",
+                               "sample": f"one problem of the sweep, 2000 steps (FP64 numpy, one "
+                                         f"core), {secs:.2f} s"}
+    return out
+
+
 METRIC = "Gpoint-steps/s at 512^3 (FP32 vs FP64, same GB300); p50/p99 serve latency"
 
 
@@ -379,6 +458,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--no-radial", action="store_true", help="skip the batched radial leg")
     ap.add_argument("--schedule", type=int, default=None, choices=[0, 1],
                     help="0: one kernel per RK stage, 1: two fused stage pairs per step "
                          "(default: the autotuner's choice, else 1)")
@@ -481,6 +561,9 @@ def main():
 
     if not args.no_serve:
         line["serve"] = serve_leg(hbe, args.serve_requests)
+
+    if not args.no_radial:
+        line["radial"] = radial_leg(hbe, torch, cpu=(rank == 0 and not args.no_cpu))
 
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(prob, 2)

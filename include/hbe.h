@@ -216,6 +216,49 @@ const char *hbe_status_string(int status);
 /* Number of stage-kernel launches this context (or batch) has enqueued. */
 int64_t hbe_launch_count(const hbe_ctx *ctx);
 
+/* ---- Radial solutions (Sec. 2.2, Eq. radial) ---------------------------- */
+/* Largest n hbe_radial_run accepts for precision prec (HBE_FP64 or HBE_FP32;
+ * 0 for any other value). */
+int hbe_radial_max_n(int prec);
+
+/* Integrates a batch of radially symmetric problems, each
+ *     phi_tt - e^{-2t} (phi_rr + (2/r) phi_r) + 3 phi_t = mu^2 phi - lambda phi^3
+ * on 0 <= r <= R with phi_r(0) = 0 and phi(R) = 0 (the paper's Eq. radial with
+ * r in (0, 1) and the factor 1/L^2 is R = L in these physical units).
+ * Discretisation (Sec. 2.2): nodes r_i = i R/n, unknowns i = 0 .. n-1; the
+ * fourth-order second difference of Sec. 2.1 and the fourth-order central first
+ * difference in the interior; the ghosts phi(-r) = phi(r) at the origin and zero
+ * from the wall on; at r = 0 the operator is 3 phi_rr(0) (L'Hospital) with the
+ * even closure (-5/2 phi_0 + 8/3 phi_1 - 1/6 phi_2)/dr^2.  Classic RK4 in time,
+ * stage times as for hbe_step, t_n = t0 + n dt.
+ *
+ * All array arguments are DEVICE pointers owned by the caller:
+ *   d_mu, d_lambda       [batch] doubles: each problem's mu and lambda;
+ *   d_phi0, d_phi1       [batch][n] doubles: phi and phi_t at the nodes at t0;
+ *   d_phi, d_psi         [batch][n] doubles, written: phi and phi_t after the
+ *                        last step taken (may not alias the inputs);
+ *   d_records            [batch][nsteps / record_every][3] doubles, written
+ *                        after every record_every-th step: t, max|phi|, and the
+ *                        number of strict sign changes of phi along r with
+ *                        |phi| <= eps ignored (each is a spherical shell where
+ *                        the solution changes sign).  Needed only when
+ *                        record_every > 0 and nsteps >= record_every;
+ *   d_steps (int64), d_status (int32)   [batch], optional (NULL): steps taken
+ *                        and 0 (all steps), 1 (max|phi| passed stop > 0) or 2
+ *                        (phi not finite); a problem ends after the first such
+ *                        step, the others keep going.
+ * prec: HBE_FP64, or HBE_FP32 (state and arithmetic in binary32, t and the
+ * stage coefficients formed in binary64).  4 <= n <= hbe_radial_max_n(prec).
+ * stop = 0 disables the threshold; non-finite values always end a problem.
+ * One CTA per problem integrates all steps on chip.  Asynchronous on `stream`
+ * (cudaStream_t, NULL = legacy default); returns HBE_EINVAL for bad arguments
+ * (nothing is launched) and HBE_ECUDA if the launch fails. */
+hbe_status hbe_radial_run(int batch, int n, double R, const double *d_mu, const double *d_lambda,
+                          const double *d_phi0, const double *d_phi1, double t0, double dt,
+                          int64_t nsteps, int prec, int record_every, double stop, double eps,
+                          double *d_phi, double *d_psi, double *d_records, int64_t *d_steps,
+                          int32_t *d_status, void *stream);
+
 /* ---- Stepping without device allocation -------------------------------- */
 /* The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory at the moment they step a problem: code that

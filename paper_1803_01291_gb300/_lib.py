@@ -24,6 +24,7 @@ EXPORTS = (
     "hbe_last_error", "hbe_status_string", "hbe_launch_count", "hbe_batch_create",
     "hbe_batch_destroy", "hbe_batch_add", "hbe_batch_remove", "hbe_batch_run",
     "hbe_batch_size", "hbe_batch_last_error", "hbe_batch_launch_count", "hbe_step_fp64_noalloc",
+    "hbe_radial_max_n", "hbe_radial_run",
 )
 
 
@@ -112,6 +113,9 @@ def load() -> ctypes.CDLL:
             "hbe_batch_last_error": (ctypes.c_char_p, [P]),
             "hbe_batch_launch_count": (I64, [P]),
             "hbe_step_fp64_noalloc": (I, [I, D, D, D, I, P, P, D, D, I64, P, P, P]),
+            "hbe_radial_max_n": (I, [I]),
+            "hbe_radial_run": (I, [I, I, D, P, P, P, P, D, D, I64, I, I, D, D, P, P, P, P, P,
+                                   P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libhbe.so")
 BUILD = os.path.join(PKG, "_build")
 
-SOURCES = ["hbe_api.cu", "hbe_aux.cu", "hbe_noalloc.cu", "hbe_stage_fp64.cu",
+SOURCES = ["hbe_api.cu", "hbe_aux.cu", "hbe_noalloc.cu", "hbe_radial.cu", "hbe_stage_fp64.cu",
            "hbe_stage_fp32.cu", "hbe_stage_bf16.cu", "hbe_stage_fp32_plain.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
