@@ -12,7 +12,7 @@
 // stages are kept; the stage arguments are rebuilt from p, q and G).
 //
 // One CTA integrates one problem of the batch for all its steps: the state
-// (p, q, G1..G3) of a thread's nodes lives in registers, the stage argument of
+// (p, q, G1..G3) of a thread's 8 nodes lives in registers, the stage argument of
 // every node (with its ghosts) in one of two shared-memory buffers, so a step
 // costs four block barriers and no global-memory traffic.  The stage
 // coefficients e^{-2 t_s} / dr^2 are computed in double precision, 64 steps at
@@ -90,8 +90,10 @@ __device__ __forceinline__ void put(T *A, int i, T v) {
   if (i == 2) A[0] = v;
 }
 
-template <typename T, int NPT>
-__global__ void __launch_bounds__(kMaxThreads, 1) radial_kernel(Args a) {
+// NPT nodes a thread (node i = thread + j x blockDim), at most TH threads, MINB
+// CTAs per SM the registers must allow
+template <typename T, int NPT, int TH, int MINB>
+__global__ void __launch_bounds__(TH, MINB) radial_kernel(Args a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shared<T> &sh = *reinterpret_cast<Shared<T> *>(smem_raw);
   T *A0 = reinterpret_cast<T *>(smem_raw + ((sizeof(Shared<T>) + 15) / 16) * 16);
@@ -256,13 +258,15 @@ size_t smem_bytes(int n) {
   return ((sizeof(Shared<T>) + 15) / 16) * 16 + 2 * (size_t)(n + 4) * sizeof(T);
 }
 
-template <typename T, int NPT>
-cudaError_t launch(const Args &a, int batch, int threads, cudaStream_t st) {
+template <typename T, int NPT, int TH, int MINB>
+cudaError_t launch(const Args &a, int batch, cudaStream_t st) {
+  const int threads = std::max(32, ((a.n + NPT - 1) / NPT + 31) / 32 * 32);
+  if (threads > TH) return cudaErrorInvalidConfiguration;
   const size_t sm = smem_bytes<T>(a.n);
-  cudaError_t e = cudaFuncSetAttribute(radial_kernel<T, NPT>,
+  cudaError_t e = cudaFuncSetAttribute(radial_kernel<T, NPT, TH, MINB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  radial_kernel<T, NPT><<<batch, threads, sm, st>>>(a);
+  radial_kernel<T, NPT, TH, MINB><<<batch, threads, sm, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -305,18 +309,14 @@ extern "C" hbe_status hbe_radial_run(int batch, int n, double R, const double *d
   a.steps = d_steps;
   a.status = d_status;
   if (a.nrec > 0 && !d_records) return HBE_EINVAL;
-  const int npt = n <= 2 * kMaxThreads ? 2 : (n <= 4 * kMaxThreads ? 4 : 8);
-  const int threads = std::max(32, ((n + npt - 1) / npt + 31) / 32 * 32);
+  // 8 nodes a thread; up to 2048 nodes a CTA of <= 256 threads, two CTAs per SM
+  // for FP32 (measured 1.3x over one CTA of 512 threads with 4 nodes each;
+  // FP64 is bound by the FP64 pipe either way)
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if (prec == HBE_FP64) {
-    e = npt == 2 ? launch<double, 2>(a, batch, threads, st)
-                 : (npt == 4 ? launch<double, 4>(a, batch, threads, st)
-                             : launch<double, 8>(a, batch, threads, st));
-  } else {
-    e = npt == 2 ? launch<float, 2>(a, batch, threads, st)
-                 : (npt == 4 ? launch<float, 4>(a, batch, threads, st)
-                             : launch<float, 8>(a, batch, threads, st));
-  }
+  if (prec == HBE_FP64)
+    e = n <= 2048 ? launch<double, 8, 256, 1>(a, batch, st) : launch<double, 8, 512, 1>(a, batch, st);
+  else
+    e = n <= 2048 ? launch<float, 8, 256, 2>(a, batch, st) : launch<float, 8, 512, 1>(a, batch, st);
   return e == cudaSuccess ? HBE_OK : HBE_ECUDA;
 }
