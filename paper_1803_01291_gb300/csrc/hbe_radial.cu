@@ -11,12 +11,13 @@
 // Time: classic RK4 in the recompute form (only the psi-components G_s of the
 // stages are kept; the stage arguments are rebuilt from p, q and G).
 //
-// One CTA integrates one problem of the batch for all its steps: the state
-// (p, q, G1..G3) of a thread's 8 nodes lives in registers, the stage argument of
-// every node (with its ghosts) in one of two shared-memory buffers, so a step
-// costs four block barriers and no global-memory traffic.  The stage
-// coefficients e^{-2 t_s} / dr^2 are computed in double precision, 64 steps at
-// a time, into shared memory.
+// One CTA integrates one problem of the batch for all its steps.  Each thread
+// owns 8 consecutive nodes and keeps their state (p, q, G1..G3) and stage
+// arguments in registers; the two neighbours on each side come from the
+// adjacent lanes by warp shuffles and, at warp boundaries, through a small
+// exchange in shared memory, so a step costs four block barriers and no
+// global-memory traffic.  The stage coefficients e^{-2 t_s} / dr^2 are computed
+// in double precision, 64 steps at a time, into shared memory.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -47,6 +48,9 @@ struct Args {
 template <typename T>
 struct Shared {
   double coef[kCoefChunk][4];
+  // stage-argument values at the ends of each warp's run of nodes, double
+  // buffered by stage: [buffer][0: last two nodes, 1: first two][warp][2]
+  T edge[2][2][kMaxThreads / 32][2];
   T wmax[kMaxThreads / 32];
   int first[kMaxThreads], last[kMaxThreads], changes[kMaxThreads];
   int any_nonfinite;
@@ -66,182 +70,185 @@ __device__ __forceinline__ T rhs_g(T Q, T c, T lap, T P, T mu2, T lam) {
   return fm(c, lap, fm(T(-3), Q, P * fm(-lam, P2, mu2)));
 }
 
-// Laplacian of the stage argument A (node i at A[i + 2]) times dr^2:
-// D2 + (2/i) D1 in the interior, 3 x the even closure at the origin.  The
-// weights of D2 and of the closure sum to zero, so both are formed from
-// differences to the centre value (same operator in exact arithmetic; in FP32
-// it avoids the cancellation of terms 1/dr^2 times larger than the result).
+// Laplacian times dr^2 at node i from the stage argument at nodes i-2 .. i+2:
+// D2 + (2/i) D1 in the interior, 3 x the even closure at the origin (where
+// p1, p2 are the values at nodes 1 and 2).  The weights of D2 and of the
+// closure sum to zero, so both are formed from differences to the centre
+// value (same operator in exact arithmetic; in FP32 it avoids the
+// cancellation of terms 1/dr^2 times larger than the result).
 template <typename T>
-__device__ __forceinline__ T lap_dr2(const T *A, int i, T two_over_i) {
-  const T c0 = A[i + 2];
-  if (i == 0)
-    return T(3) * fm(T(8.0 / 3.0), A[3] - c0, T(-1.0 / 6.0) * (A[4] - c0));
-  const T m2 = A[i], m1 = A[i + 1], p1 = A[i + 3], p2 = A[i + 4];
+__device__ __forceinline__ T lap_dr2(T m2, T m1, T c0, T p1, T p2, bool origin, T two_over_i) {
+  if (origin) return T(3) * fm(T(8.0 / 3.0), p1 - c0, T(-1.0 / 6.0) * (p2 - c0));
   const T d2 = fm(T(-1.0 / 12.0), (m2 - c0) + (p2 - c0), T(4.0 / 3.0) * ((m1 - c0) + (p1 - c0)));
   const T d1 = fm(T(2.0 / 3.0), p1 - m1, T(-1.0 / 12.0) * (p2 - m2));
   return fm(two_over_i, d1, d2);
 }
 
-// store a node's stage argument, and the mirrored ghost for nodes 1 and 2
-template <typename T>
-__device__ __forceinline__ void put(T *A, int i, T v) {
-  A[i + 2] = v;
-  if (i == 1) A[1] = v;
-  if (i == 2) A[0] = v;
-}
-
-// NPT nodes a thread (node i = thread + j x blockDim), at most TH threads, MINB
-// CTAs per SM the registers must allow
-template <typename T, int NPT, int TH, int MINB>
+// Thread t owns the V consecutive nodes V t .. V t + V - 1 (those below n) and
+// keeps their state in registers; a stage's neighbour values come from the
+// adjacent lanes by shuffles and, across warps, from the `edge` exchange in
+// shared memory, behind one block barrier per stage.  TH: most threads a
+// block, MINB: CTAs per SM the registers must allow.
+template <typename T, int V, int TH, int MINB>
 __global__ void __launch_bounds__(TH, MINB) radial_kernel(Args a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Shared<T> &sh = *reinterpret_cast<Shared<T> *>(smem_raw);
-  T *A0 = reinterpret_cast<T *>(smem_raw + ((sizeof(Shared<T>) + 15) / 16) * 16);
-  T *A1 = A0 + (a.n + 4);
-  const int n = a.n, tid = threadIdx.x, nt = blockDim.x, b = blockIdx.x;
+  static_assert(V >= 3, "the origin mirror reads nodes 1 and 2 from thread 0");
+  __shared__ Shared<T> sh;
+  const int n = a.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = blockDim.x >> 5, b = blockIdx.x, i0 = tid * V;
+  const unsigned full = 0xffffffffu;
   const T mu2 = T(a.mu[b] * a.mu[b]), lam = T(a.lambda[b]);
   const T dt = T(a.dt), hdt = T(0.5 * a.dt), qdt2 = T(0.25 * a.dt * a.dt),
           hdt2 = T(0.5 * a.dt * a.dt), sdt2 = T(a.dt * a.dt / 6.0), sdt = T(a.dt / 6.0);
 
-  T p[NPT], q[NPT], g1[NPT], g2[NPT], g3[NPT], w[NPT];
+  // nodes at or beyond n hold 0 in every field: the wall value and its ghosts
+  T p[V], q[V], g1[V], g2[V], g3[V], w[V];
 #pragma unroll
-  for (int j = 0; j < NPT; ++j) {
-    const int i = tid + j * nt;
+  for (int j = 0; j < V; ++j) {
+    const int i = i0 + j;
     p[j] = q[j] = g1[j] = g2[j] = g3[j] = T(0);
     w[j] = i > 0 ? T(2.0 / (double)i) : T(0);
     if (i < n) {
       p[j] = T(a.phi0[(size_t)b * n + i]);
       q[j] = T(a.phi1[(size_t)b * n + i]);
-      put(A0, i, p[j]);
     }
   }
-  if (tid == 0) {
-    A0[n + 2] = A0[n + 3] = A1[n + 2] = A1[n + 3] = T(0);
-    sh.any_nonfinite = 0;
-  }
+  if (tid == 0) sh.any_nonfinite = 0;
+
+  // E[0 .. V+3] = stage argument at nodes i0-2 .. i0+V+1; the barrier returns
+  // the OR of `flag` over the block
+  int buf = 0;
+  auto exchange = [&](const T (&P)[V], T (&E)[V + 4], int flag) -> int {
+#pragma unroll
+    for (int j = 0; j < V; ++j) E[j + 2] = P[j];
+    if (lane == 31) { sh.edge[buf][0][warp][0] = P[V - 2]; sh.edge[buf][0][warp][1] = P[V - 1]; }
+    if (lane == 0) { sh.edge[buf][1][warp][0] = P[0]; sh.edge[buf][1][warp][1] = P[1]; }
+    T l2 = __shfl_up_sync(full, P[V - 2], 1), l1 = __shfl_up_sync(full, P[V - 1], 1);
+    T r1 = __shfl_down_sync(full, P[0], 1), r2 = __shfl_down_sync(full, P[1], 1);
+    const int any = __syncthreads_or(flag);
+    if (lane == 0) {
+      if (warp > 0) { l2 = sh.edge[buf][0][warp - 1][0]; l1 = sh.edge[buf][0][warp - 1][1]; }
+      else { l2 = P[2]; l1 = P[1]; }  // phi(-r) = phi(r) at the origin
+    }
+    if (lane == 31) {
+      if (warp + 1 < nw) { r1 = sh.edge[buf][1][warp + 1][0]; r2 = sh.edge[buf][1][warp + 1][1]; }
+      else { r1 = r2 = T(0); }
+    }
+    E[0] = l2; E[1] = l1; E[V + 2] = r1; E[V + 3] = r2;
+    buf ^= 1;
+    return any;
+  };
+  auto lap = [&](const T (&E)[V + 4], int j) -> T {
+    return lap_dr2(E[j], E[j + 1], E[j + 2], E[j + 3], E[j + 4], tid == 0 && j == 0, w[j]);
+  };
 
   int64_t k = 0;
-  int status = 0;
+  int status = 0, flag = 0, bad = 0;
+  int64_t pending = 0;  // 1 + index of a record whose partial results await combining
   const double inv_dr2 = 1.0 / (a.dr * a.dr);
-  for (; k < a.nsteps; ++k) {
+  T E[V + 4], P[V];
+  for (;; ++k) {
     const int kc = (int)(k % kCoefChunk);
-    if (kc == 0) {
-      // table e^{-2 t_s} / dr^2 for the next steps (t_n = t0 + n dt, Sec. 2.1)
-      for (int e = tid; e < 4 * kCoefChunk; e += nt) {
+    if (kc == 0 && k < a.nsteps) {
+      // table e^{-2 t_s} / dr^2 for the next steps (t_n = t0 + n dt, Sec. 2.1);
+      // the barrier of the exchange below publishes it
+      for (int e = tid; e < 4 * kCoefChunk; e += blockDim.x) {
         const int s = e & 3, kk = e >> 2;
         const double t = a.t0 + (double)(k + kk) * a.dt;
         const double ts = s == 0 ? t : (s == 3 ? t + a.dt : t + a.dt / 2);
         sh.coef[kk][s] = exp(-2.0 * ts) * inv_dr2;
       }
-      __syncthreads();
     }
+    // stage 1 exchange; its barrier also ends step k - 1 (stop rule, records)
+    const int any = exchange(p, E, flag);
+    if (pending && tid == 0) {
+      T mm = T(0);
+      for (int wi = 0; wi < nw; ++wi) mm = tmax(mm, sh.wmax[wi]);
+      int prev = 0, total = 0;
+      for (int t = 0; t < (int)blockDim.x; ++t) {
+        total += sh.changes[t];
+        if (sh.first[t] != 0) {
+          if (prev != 0 && prev != sh.first[t]) ++total;
+          prev = sh.last[t];
+        }
+      }
+      double *rec = a.records + ((size_t)b * a.nrec + (pending - 1)) * 3;
+      rec[0] = a.t0 + (double)k * a.dt;
+      rec[1] = (double)mm;
+      rec[2] = (double)total;
+    }
+    pending = 0;
+    if (any) {
+      status = sh.any_nonfinite ? 2 : 1;
+      break;
+    }
+    if (k >= a.nsteps) break;
     const T c1 = T(sh.coef[kc][0]), c2 = T(sh.coef[kc][1]), c3 = T(sh.coef[kc][2]),
             c4 = T(sh.coef[kc][3]);
-    // stage 1: argument p (A0) -> G1; forms P2 = p + dt/2 q into A1
+    // stage 1: argument p -> G1
 #pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-      const int i = tid + j * nt;
-      if (i < n) {
-        const T P = p[j];
-        g1[j] = rhs_g(q[j], c1, lap_dr2(A0, i, w[j]), P, mu2, lam);
-        put(A1, i, fm(hdt, q[j], p[j]));
-      }
-    }
-    __syncthreads();
-    // stage 2: argument P2 (A1), Q2 = q + dt/2 G1 -> G2; forms P3 into A0
+    for (int j = 0; j < V; ++j)
+      if (i0 + j < n) g1[j] = rhs_g(q[j], c1, lap(E, j), p[j], mu2, lam);
+    // stage 2: argument P2 = p + dt/2 q, Q2 = q + dt/2 G1 -> G2
 #pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-      const int i = tid + j * nt;
-      if (i < n) {
-        const T P = A1[i + 2], Q = fm(hdt, g1[j], q[j]);
-        g2[j] = rhs_g(Q, c2, lap_dr2(A1, i, w[j]), P, mu2, lam);
-        put(A0, i, fm(qdt2, g1[j], fm(hdt, q[j], p[j])));
-      }
-    }
-    __syncthreads();
-    // stage 3: argument P3 (A0), Q3 = q + dt/2 G2 -> G3; forms P4 into A1
+    for (int j = 0; j < V; ++j) P[j] = fm(hdt, q[j], p[j]);
+    exchange(P, E, 0);
 #pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-      const int i = tid + j * nt;
-      if (i < n) {
-        const T P = A0[i + 2], Q = fm(hdt, g2[j], q[j]);
-        g3[j] = rhs_g(Q, c3, lap_dr2(A0, i, w[j]), P, mu2, lam);
-        put(A1, i, fm(hdt2, g2[j], fm(dt, q[j], p[j])));
-      }
-    }
-    __syncthreads();
-    // stage 4: argument P4 (A1), Q4 = q + dt G3 -> G4; RK4 combine; p' into A0
+    for (int j = 0; j < V; ++j)
+      if (i0 + j < n) g2[j] = rhs_g(fm(hdt, g1[j], q[j]), c2, lap(E, j), P[j], mu2, lam);
+    // stage 3: argument P3 = p + dt/2 q + dt^2/4 G1, Q3 = q + dt/2 G2 -> G3
+#pragma unroll
+    for (int j = 0; j < V; ++j) P[j] = fm(qdt2, g1[j], fm(hdt, q[j], p[j]));
+    exchange(P, E, 0);
+#pragma unroll
+    for (int j = 0; j < V; ++j)
+      if (i0 + j < n) g3[j] = rhs_g(fm(hdt, g2[j], q[j]), c3, lap(E, j), P[j], mu2, lam);
+    // stage 4: argument P4 = p + dt q + dt^2/2 G2, Q4 = q + dt G3 -> G4; RK4 combine
+#pragma unroll
+    for (int j = 0; j < V; ++j) P[j] = fm(hdt2, g2[j], fm(dt, q[j], p[j]));
+    exchange(P, E, 0);
     T lmax = T(0);
-    int bad = 0;
 #pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-      const int i = tid + j * nt;
-      if (i < n) {
-        const T P = A1[i + 2], Q = fm(dt, g3[j], q[j]);
-        const T g4 = rhs_g(Q, c4, lap_dr2(A1, i, w[j]), P, mu2, lam);
+    for (int j = 0; j < V; ++j) {
+      if (i0 + j < n) {
+        const T g4 = rhs_g(fm(dt, g3[j], q[j]), c4, lap(E, j), P[j], mu2, lam);
         const T s3 = g1[j] + g2[j] + g3[j];
         p[j] = fm(sdt2, s3, fm(dt, q[j], p[j]));
         q[j] = fm(sdt, fm(T(2), g2[j] + g3[j], g1[j] + g4), q[j]);
-        put(A0, i, p[j]);
         const T m = fabs(p[j]);
         if (!(m <= m) || isinf(m)) bad = 1;  // NaN or infinite
         lmax = tmax(lmax, m);
       }
     }
-    const bool over = a.stop > 0.0 && (double)lmax > a.stop;
-    const int any = __syncthreads_or(bad || over);
+    if (bad) atomicOr(&sh.any_nonfinite, 1);
+    flag = bad || (a.stop > 0.0 && (double)lmax > a.stop);
     const int64_t done = k + 1;
-    if (a.record_every > 0 && done % a.record_every == 0) {
-      // max|phi| and the number of strict sign changes along r (|phi| <= eps ignored)
+    if (a.nrec > 0 && done % a.record_every == 0 && done / a.record_every <= a.nrec) {
+      // partial max|phi| and strict sign changes (|phi| <= eps ignored) of this
+      // thread's run of nodes; combined by thread 0 after the next barrier
       T m = lmax;
-      for (int o = 16; o > 0; o >>= 1) m = tmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if ((tid & 31) == 0) sh.wmax[tid >> 5] = m;
-      const int per = (n + nt - 1) / nt, lo = tid * per, hi = min(n, lo + per);
+      for (int o = 16; o > 0; o >>= 1) m = tmax(m, __shfl_xor_sync(full, m, o));
+      if (lane == 0) sh.wmax[warp] = m;
       int f = 0, l = 0, c = 0;
-      for (int i = lo; i < hi; ++i) {
-        const double v = (double)A0[i + 2];
-        const int s = v > a.eps ? 1 : (v < -a.eps ? -1 : 0);
-        if (s == 0) continue;
-        if (f == 0) f = s;
-        else if (s != l) ++c;
-        l = s;
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        if (i0 + j >= n) continue;
+        const double v = (double)p[j];
+        const int sg = v > a.eps ? 1 : (v < -a.eps ? -1 : 0);
+        if (sg == 0) continue;
+        if (f == 0) f = sg;
+        else if (sg != l) ++c;
+        l = sg;
       }
       sh.first[tid] = f;
       sh.last[tid] = l;
       sh.changes[tid] = c;
-      __syncthreads();
-      if (tid == 0) {
-        T mm = T(0);
-        for (int wi = 0; wi < (nt + 31) / 32; ++wi) mm = tmax(mm, sh.wmax[wi]);
-        int prev = 0, total = 0;
-        for (int t = 0; t < nt; ++t) {
-          total += sh.changes[t];
-          if (sh.first[t] != 0) {
-            if (prev != 0 && prev != sh.first[t]) ++total;
-            prev = sh.last[t];
-          }
-        }
-        const int64_t r = done / a.record_every - 1;
-        if (a.records && r < a.nrec) {
-          double *rec = a.records + ((size_t)b * a.nrec + r) * 3;
-          rec[0] = a.t0 + (double)done * a.dt;
-          rec[1] = (double)mm;
-          rec[2] = (double)total;
-        }
-      }
-    }
-    if (any) {
-      if (bad) atomicOr(&sh.any_nonfinite, 1);
-      __syncthreads();
-      status = sh.any_nonfinite ? 2 : 1;
-      ++k;
-      break;
+      pending = done / a.record_every;
     }
   }
 
 #pragma unroll
-  for (int j = 0; j < NPT; ++j) {
-    const int i = tid + j * nt;
+  for (int j = 0; j < V; ++j) {
+    const int i = i0 + j;
     if (i < n) {
       a.phi[(size_t)b * n + i] = (double)p[j];
       a.psi[(size_t)b * n + i] = (double)q[j];
@@ -253,20 +260,11 @@ __global__ void __launch_bounds__(TH, MINB) radial_kernel(Args a) {
   }
 }
 
-template <typename T>
-size_t smem_bytes(int n) {
-  return ((sizeof(Shared<T>) + 15) / 16) * 16 + 2 * (size_t)(n + 4) * sizeof(T);
-}
-
-template <typename T, int NPT, int TH, int MINB>
+template <typename T, int V, int TH, int MINB>
 cudaError_t launch(const Args &a, int batch, cudaStream_t st) {
-  const int threads = std::max(32, ((a.n + NPT - 1) / NPT + 31) / 32 * 32);
+  const int threads = std::max(32, ((a.n + V - 1) / V + 31) / 32 * 32);
   if (threads > TH) return cudaErrorInvalidConfiguration;
-  const size_t sm = smem_bytes<T>(a.n);
-  cudaError_t e = cudaFuncSetAttribute(radial_kernel<T, NPT, TH, MINB>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  radial_kernel<T, NPT, TH, MINB><<<batch, threads, sm, st>>>(a);
+  radial_kernel<T, V, TH, MINB><<<batch, threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -309,9 +307,7 @@ extern "C" hbe_status hbe_radial_run(int batch, int n, double R, const double *d
   a.steps = d_steps;
   a.status = d_status;
   if (a.nrec > 0 && !d_records) return HBE_EINVAL;
-  // 8 nodes a thread; up to 2048 nodes a CTA of <= 256 threads, two CTAs per SM
-  // for FP32 (measured 1.3x over one CTA of 512 threads with 4 nodes each;
-  // FP64 is bound by the FP64 pipe either way)
+  // 8 nodes a thread: up to 2048 nodes a CTA of <= 256 threads, two CTAs per SM
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (prec == HBE_FP64)
