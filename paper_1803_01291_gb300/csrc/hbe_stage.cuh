@@ -35,7 +35,6 @@
 #pragma once
 #include <cuda_bf16.h>
 
-#include <type_traits>
 
 #include "hbe_common.cuh"
 
@@ -127,9 +126,6 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
 __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
                "r"(bytes)
@@ -211,10 +207,6 @@ __device__ __forceinline__ void store_as(T *p, const TM (&v)[n]) {
   for (int j = 0; j < n; ++j) e[j] = narrow<T>(v[j]);
   *reinterpret_cast<R *>(p) = raw;
 }
-template <class TM, int n>
-__device__ __forceinline__ void lds(const TM *p, TM (&v)[n]) { load_as<TM, TM, n>(p, v); }
-template <class TM, int n>
-__device__ __forceinline__ void sts(TM *p, const TM (&v)[n]) { store_as<TM, TM, n>(p, v); }
 
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -546,26 +538,19 @@ struct Consumer {
 
   // One z-plane: plane m of the item enters the window (slot `slot`); for
   // m >= 4 the output plane m - 4 (loaded as plane m - 2, slot s2) is computed.
-  // Window index of plane j is j mod 5, and m mod 5 == ROT.
-  template <int ROT>
+  // The window is shifted by one plane first; the newest plane is at index 4.
   __device__ __forceinline__ void plane(const Item &it, int m, int slot, int s2,
                                         TM (&win)[5][KN][VY][VEC], TM &run_max,
                                         bool &bad) const {
-    // ROT < 0: the window is shifted by one plane first and the newest plane
-    // lives at index 4; otherwise plane j lives at index j mod 5 (ROT = m mod 5).
-    constexpr int R0 = ROT < 0 ? 4 : ROT;
-    constexpr int W0 = R0 % 5, WM1 = (R0 + 4) % 5, WM2 = (R0 + 3) % 5, WM3 = (R0 + 2) % 5,
-                  WM4 = (R0 + 1) % 5;
-    if constexpr (ROT < 0) {
+    constexpr int W0 = 4, WM1 = 3, WM2 = 2, WM3 = 1, WM4 = 0;
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int kk = 0; kk < KN; ++kk)
+      for (int kk = 0; kk < KN; ++kk)
 #pragma unroll
-          for (int r = 0; r < VY; ++r)
+        for (int r = 0; r < VY; ++r)
 #pragma unroll
-            for (int j = 0; j < VEC; ++j) win[a][kk][r][j] = win[a + 1][kk][r][j];
-    }
+          for (int j = 0; j < VEC; ++j) win[a][kk][r][j] = win[a + 1][kk][r][j];
     const unsigned char *base = ring + slot * C::SLOT_BYTES;
 #pragma unroll
     for (int r = 0; r < VY; ++r) {
@@ -787,7 +772,7 @@ struct Consumer {
       TM run_max = (TM)0;
       bool bad = false;
       // one plane: wait for its slot, compute, release what is no longer needed
-      auto step = [&](auto rot, int m) -> bool {
+      auto step = [&](int m) -> bool {
         if (!mbar_wait_bounded(&full[slot], phase)) {
           *abort_flag = 1;
           atomicOr(prm.err, (unsigned)DEV_ERR_TIMEOUT);
@@ -795,7 +780,7 @@ struct Consumer {
         }
         if (*abort_flag) return false;
         const int s2 = slot >= 2 ? slot - 2 : slot + RING - 2;  // slot of plane m - 2
-        self.template plane<decltype(rot)::value>(it, m, slot, s2, win, run_max, bad);
+        self.plane(it, m, slot, s2, win, run_max, bad);
         __syncwarp();
         if (self.lane == 0) {
           if (m < 2 || m >= it.nplanes - 2) mbar_arrive(&empty[slot]);
@@ -805,7 +790,7 @@ struct Consumer {
         return true;
       };
       bool ok = true;
-      for (int m = 0; ok && m < it.nplanes; ++m) ok = step(std::integral_constant<int, -1>{}, m);
+      for (int m = 0; ok && m < it.nplanes; ++m) ok = step(m);
       if (!ok) return;
       if constexpr (S == 4 || S == 6) {
         double v = (double)run_max;
