@@ -221,7 +221,8 @@ __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
 }
 
 // Store VEC values of a field at interior point (x, y) of a plane of the padded
-// layout (`row` points at the row's x = 0).  `ragged`: the tile may cross x = N
+// layout (`row` points at the row's x = 0), and for periodic problems the ghost
+// rows beyond the y edges (`edge`).  `ragged`: the tile may cross x = N
 // (mask); `edge`: periodic tile touching a wrap band (write the ghost copies).
 template <class T, class TM, int VEC>
 __device__ __forceinline__ void store_point(T *row, int64_t pitch, int N, bool ragged, bool edge,
@@ -239,10 +240,29 @@ __device__ __forceinline__ void store_point(T *row, int64_t pitch, int N, bool r
       const int xx = x + j;
       if (xx >= N) continue;
       const T val = narrow<T>(v[j]);
-      if (xx < 2) row[xx + N] = val;
-      if (xx >= N - 2) row[xx - N] = val;
       if (y < 2) row[(int64_t)N * pitch + xx] = val;
       if (y >= N - 2) row[-(int64_t)N * pitch + xx] = val;
+    }
+  }
+}
+
+// Periodic x ghosts: columns N, N+1 copy x = 0, 1 and columns -2, -1 copy
+// x = N-2, N-1, written by the lanes that hold those points (`p` points at the
+// lane's first point).  `vec`: N is a multiple of VEC, so each such lane copies
+// its whole vector with one aligned store (the extra columns are the wrapped
+// values too); the store is predicated, so the warp does not branch.
+template <class T, class TM, int VEC>
+__device__ __forceinline__ void store_xghost(T *p, int N, int x, bool on, bool vec,
+                                             const TM (&v)[VEC]) {
+  if (vec) {
+    T *g = x < 2 ? p + N : p - N;
+    if (on) store_as<T, TM, VEC>(g, v);
+  } else if (on) {
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      const int xx = x + j;
+      if (xx < 2) p[j + N] = narrow<T>(v[j]);
+      else if (xx >= N - 2 && xx < N) p[j - N] = narrow<T>(v[j]);
     }
   }
 }
@@ -529,7 +549,7 @@ struct Consumer {
 
   struct Item {
     int N, x, z0, nplanes, set;
-    bool periodic, ragged, lane_edge, xok;
+    bool periodic, ragged, lane_edge, xok, xg_vec;
     int64_t pitch_s, plane_s, pitch_g, plane_g, row_s, row_g;
     int y0;
     TG *outG0, *outG1;
@@ -642,7 +662,7 @@ struct Consumer {
         }
       }
       const bool rok = it.xok && y < it.N;
-      const bool edge = it.lane_edge || (it.periodic && (y < 2 || y >= it.N - 2));
+      const bool edge = it.periodic && (y < 2 || y >= it.N - 2);
       const bool fast = rok && !it.ragged && !edge;
       if constexpr (S <= 3 || S == 5) {
         const int64_t off = (int64_t)z * it.plane_g + it.row_g + r * it.pitch_g;
@@ -653,6 +673,12 @@ struct Consumer {
           store_point<TG, TM, VEC>(it.outG0 + off - it.x, it.pitch_g, it.N, it.ragged, edge, it.x, y, res[0]);
           if constexpr (S == 5)
             store_point<TG, TM, VEC>(it.outG1 + off - it.x, it.pitch_g, it.N, it.ragged, edge, it.x, y, res[KN - 1]);
+        }
+        if (it.periodic) {
+          const bool on = it.lane_edge && rok;
+          store_xghost<TG, TM, VEC>(it.outG0 + off, it.N, it.x, on, it.xg_vec, res[0]);
+          if constexpr (S == 5)
+            store_xghost<TG, TM, VEC>(it.outG1 + off, it.N, it.x, on, it.xg_vec, res[KN - 1]);
         }
       } else {
         // RK4 combine (Sec. 2.1): p' = p + dt q + dt^2/6 (G1 + G2 + G3),
@@ -698,6 +724,15 @@ struct Consumer {
             store_point<TS, TM, VEC>(it.outQL + off - it.x, it.pitch_s, it.N, it.ragged, edge, it.x, y, ql);
           }
         }
+        if (it.periodic) {
+          const bool on = it.lane_edge && rok;
+          store_xghost<TS, TM, VEC>(it.outP + off, it.N, it.x, on, it.xg_vec, pn);
+          store_xghost<TS, TM, VEC>(it.outQ + off, it.N, it.x, on, it.xg_vec, qn);
+          if constexpr (C::KAHAN) {
+            store_xghost<TS, TM, VEC>(it.outPL + off, it.N, it.x, on, it.xg_vec, pl);
+            store_xghost<TS, TM, VEC>(it.outQL + off, it.N, it.x, on, it.xg_vec, ql);
+          }
+        }
       }
     }
     (void)bad;
@@ -741,6 +776,7 @@ struct Consumer {
       it.xok = it.x < it.N;
       // periodic ghost copies are written only by the lanes / rows next to a wrap
       it.lane_edge = it.periodic && (it.x < 2 || it.x + VEC > it.N - 2);
+      it.xg_vec = it.N % VEC == 0;
       it.pitch_s = d->pitch_s; it.plane_s = d->plane_s;
       it.pitch_g = d->pitch_g; it.plane_g = d->plane_g;
       it.row_s = (int64_t)(it.y0 + self.ly0 + 2) * it.pitch_s + HXS + it.x;
