@@ -108,6 +108,7 @@ struct hbe_batch {
   unsigned *d_err = nullptr;
   cudaGraphExec_t gexec = nullptr;
   bool dirty = true;
+  bool wraps = false;  // the captured graph has the periodic ghost copies
   int64_t launches = 0;
   std::string err;
 };
@@ -280,6 +281,16 @@ hbe_status launch_stage(std::string &err, const KernelInfo &ki, int grid, const 
   return HBE_OK;
 }
 
+// kernels one RK4 step launches: the stage kernels, and for a periodic context
+// the ghost copy after each stage whose output is read with a halo
+int launches_per_step(const hbe_ctx *ctx) {
+  const int first = ctx->schedule ? 4 : 0, last = ctx->schedule ? 6 : 4;
+  int n = last - first;
+  if (ctx->bc == HBE_BC_PERIODIC)
+    for (int s = first; s < last; ++s) n += stage_needs_wrap(s + 1) ? 1 : 0;
+  return n;
+}
+
 hbe_status ensure_graph(hbe_ctx *ctx) {
   if (ctx->gexec) return HBE_OK;
   const VariantTable &vt = table_for(ctx->prec);
@@ -291,6 +302,11 @@ hbe_status ensure_graph(hbe_ctx *ctx) {
     for (int s = first; s < last && st == HBE_OK; ++s) {
       StageParams p{ctx->d_desc, ctx->d_items, ctx->d_nitems, ctx->d_err, k};
       st = launch_stage(ctx->err, vt.k[ctx->variant][s], ctx->grid[s], p, ctx->cap_stream);
+      if (st == HBE_OK && ctx->bc == HBE_BC_PERIODIC && stage_needs_wrap(s + 1)) {
+        cudaError_t ew = launch_wrap(ctx->d_desc, ctx->d_one, 1, k, s + 1, 2 * ctx->sms,
+                                     ctx->cap_stream);
+        if (ew != cudaSuccess) st = set_err(ctx->err, HBE_ECUDA, "%s", cudaGetErrorString(ew));
+      }
     }
   cudaError_t e = launch_advance(ctx->d_desc, ctx->d_one, 1, ctx->K, ctx->cap_stream);
   cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
@@ -736,7 +752,7 @@ hbe_status hbe_step_async(hbe_ctx *ctx, int64_t nsteps, double dt) {
   }
   const int64_t runs = (nsteps + ctx->K - 1) / ctx->K;
   for (int64_t r = 0; r < runs; ++r) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
-  ctx->launches += runs * (ctx->schedule ? 2 : 4) * ctx->K;
+  ctx->launches += runs * launches_per_step(ctx) * ctx->K;
   ctx->pending = true;
   return HBE_OK;
 }
@@ -780,20 +796,27 @@ hbe_status hbe_profile_stages(hbe_ctx *ctx, int64_t nsteps, double dt, float *ms
   }
   CK(launch_set_run(ctx->d_desc, nsteps, d.t0, d.dt, d.stop_thr, 1, ctx->stream));
   const int first = ctx->schedule ? 4 : 0, nl = ctx->schedule ? 2 : 4;
-  std::vector<cudaEvent_t> ev((size_t)nsteps * (nl + 1), nullptr);
+  // events before and after each stage kernel (a periodic context's ghost copy
+  // runs after the second event and is not part of the stage's time)
+  std::vector<cudaEvent_t> ev((size_t)nsteps * nl * 2, nullptr);
   for (auto &e : ev) CK(cudaEventCreate(&e));
   const VariantTable &vt = table_for(ctx->prec);
+  int64_t wraps = 0;
   for (int64_t n = 0; n < nsteps && st == HBE_OK; ++n) {
     for (int s = 0; s < nl && st == HBE_OK; ++s) {
-      CK(cudaEventRecord(ev[n * (nl + 1) + s], ctx->stream));
+      CK(cudaEventRecord(ev[(n * nl + s) * 2], ctx->stream));
       StageParams p{ctx->d_desc, ctx->d_items, ctx->d_nitems, ctx->d_err, 0};
       st = launch_stage(ctx->err, vt.k[ctx->variant][first + s], ctx->grid[first + s], p,
                         ctx->stream);
+      CK(cudaEventRecord(ev[(n * nl + s) * 2 + 1], ctx->stream));
+      if (st == HBE_OK && ctx->bc == HBE_BC_PERIODIC && stage_needs_wrap(first + s + 1)) {
+        CK(launch_wrap(ctx->d_desc, ctx->d_one, 1, 0, first + s + 1, 2 * ctx->sms, ctx->stream));
+        ++wraps;
+      }
     }
-    CK(cudaEventRecord(ev[n * (nl + 1) + nl], ctx->stream));
     CK(launch_advance(ctx->d_desc, ctx->d_one, 1, 1, ctx->stream));
   }
-  ctx->launches += nsteps * nl;
+  ctx->launches += nsteps * nl + wraps;
   ctx->pending = true;
   hbe_status st2 = sync_ctx(ctx);
   double acc[4] = {0, 0, 0, 0};
@@ -801,7 +824,7 @@ hbe_status hbe_profile_stages(hbe_ctx *ctx, int64_t nsteps, double dt, float *ms
     for (int64_t n = 0; n < nsteps; ++n)
       for (int s = 0; s < nl; ++s) {
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev[n * (nl + 1) + s], ev[n * (nl + 1) + s + 1]);
+        cudaEventElapsedTime(&ms, ev[(n * nl + s) * 2], ev[(n * nl + s) * 2 + 1]);
         acc[s] += ms;
       }
   }
@@ -1124,6 +1147,9 @@ hbe_status hbe_batch_remove(hbe_batch *b, hbe_ctx *ctx) {
 static hbe_status batch_rebuild(hbe_batch *b) {
   const int M = (int)b->members.size();
   bool recapture = !b->gexec;
+  bool periodic = false;
+  for (hbe_ctx *c : b->members) periodic |= c->bc == HBE_BC_PERIODIC;
+  if (periodic && !b->wraps) recapture = true;
   if (M > b->cap_desc) {
     int cap = std::max(64, b->cap_desc);
     while (cap < M) cap *= 2;
@@ -1178,13 +1204,21 @@ static hbe_status batch_rebuild(hbe_batch *b) {
     hbe_status st = HBE_OK;
     // the batch always runs the fused stage pairs (kernels 4 and 5 of a variant)
     for (int k = 0; k < b->K && st == HBE_OK; ++k)
-      for (int s = 4; s < 6 && st == HBE_OK; ++s)
+      for (int s = 4; s < 6 && st == HBE_OK; ++s) {
         for (int v = 0; v < b->nvariants && st == HBE_OK; ++v) {
           auto &l = b->lists[v];
           if (!l.d_n) continue;
           StageParams p{b->d_descs, l.d_items, l.d_n, b->d_err, k};
           st = launch_stage(b->err, vt.k[v][s], l.grid[s], p, b->cap_stream);
         }
+        // ghost copies of the periodic members' outputs of this stage pair
+        if (st == HBE_OK && periodic) {
+          cudaError_t ew = launch_wrap(b->d_descs, b->d_ndesc, b->cap_desc, k, s + 1, 2 * b->sms,
+                                       b->cap_stream);
+          if (ew != cudaSuccess) st = set_err(b->err, HBE_ECUDA, "%s", cudaGetErrorString(ew));
+        }
+      }
+    b->wraps = periodic;
     cudaError_t e = launch_advance(b->d_descs, b->d_ndesc, b->cap_desc, b->K, b->cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
     if (st != HBE_OK) return st;
@@ -1210,7 +1244,7 @@ hbe_status hbe_batch_run(hbe_batch *b, hbe_ctx **finished, int max_finished, int
   CKX(b->err, cudaGraphLaunch(b->gexec, b->stream));
   int used = 0;
   for (int v = 0; v < b->nvariants; ++v) used += b->lists[v].d_n ? 1 : 0;
-  b->launches += (int64_t)2 * b->K * used;
+  b->launches += (int64_t)(2 * used + (b->wraps ? 2 : 0)) * b->K;
   CKX(b->err, cudaMemcpyAsync(b->h_descs, b->d_descs, M * sizeof(Desc), cudaMemcpyDeviceToHost,
                               b->stream));
   CKX(b->err, cudaStreamSynchronize(b->stream));
@@ -1221,7 +1255,7 @@ hbe_status hbe_batch_run(hbe_batch *b, hbe_ctx **finished, int max_finished, int
   for (int i = 0; i < M; ++i) {
     hbe_ctx *c = b->members[i];
     *c->h_desc = b->h_descs[i];
-    c->launches += (int64_t)2 * b->K;
+    c->launches += (int64_t)(c->bc == HBE_BC_PERIODIC ? 4 : 2) * b->K;
     const Desc &d = b->h_descs[i];
     if (d.n_base >= d.n_end || d.status != ST_RUNNING) {
       leave_batch(c);

@@ -174,6 +174,87 @@ cudaError_t launch_advance(Desc *descs, const int *ndesc, int max_desc, int K, c
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- periodic ghosts
+// After a stage launch of a periodic context, the ghost cells of the fields it
+// wrote that later launches read with a halo receive the wrapped copies:
+// columns -2, -1 <- N-2, N-1 and N, N+1 <- 0, 1 of every row, and rows
+// -2, -1 <- N-2, N-1 and N, N+1 <- 0, 1 of every plane (x in [0, N)).  The
+// fields: stage 1 -> G1, stage 2 -> G2, stages 4 and 6 -> phi, psi of the new
+// state, stage 5 (stages 1 + 2) -> G1, G2; G3 and the compensation parts are
+// read at the point only.  Elements are moved as raw bits.
+template <class E>
+__device__ void wrap_field(E *f, int N, int pitch, int64_t plane, int hx, long long tid,
+                           long long nth) {
+  const long long nx = (long long)N * N;
+  for (long long u = tid; u < nx; u += nth) {
+    const int z = (int)(u / N), y = (int)(u % N);
+    E *row = f + (int64_t)z * plane + (int64_t)(y + 2) * pitch + hx;
+    const E a = row[0], b = row[1], c = row[N - 2], d = row[N - 1];
+    row[-2] = c;
+    row[-1] = d;
+    row[N] = a;
+    row[N + 1] = b;
+  }
+  // padded rows 0, 1 <- N, N+1 (y = N-2, N-1) and N+2, N+3 <- 2, 3 (y = 0, 1)
+  const long long ny = (long long)N * 4 * N;
+  for (long long u = tid; u < ny; u += nth) {
+    const int x = (int)(u % N);
+    const long long r = u / N;
+    const int z = (int)(r >> 2), g = (int)(r & 3);
+    const int dst = g < 2 ? g : N + g, src = g < 2 ? N + g : g;
+    E *col = f + (int64_t)z * plane + hx + x;
+    col[(int64_t)dst * pitch] = col[(int64_t)src * pitch];
+  }
+}
+
+template <class E>
+__device__ void wrap_pair(void *a, void *b, int N, int pitch, int64_t plane, int hx, long long tid,
+                          long long nth) {
+  wrap_field<E>(static_cast<E *>(a), N, pitch, plane, hx, tid, nth);
+  if (b) wrap_field<E>(static_cast<E *>(b), N, pitch, plane, hx, tid, nth);
+}
+
+__global__ void wrap_kernel(Desc *descs, const int *ndesc, int k, int stage) {
+  if ((int)blockIdx.y >= *ndesc) return;
+  const Desc *d = descs + blockIdx.y;
+  if (d->bc != 1) return;
+  const long long n = d->n_base + k;
+  if (n >= d->n_end || __ldcg(&d->stop_k) <= k) return;  // the step was not taken
+  const int so = (int)(n & 1) ^ 1;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const int N = d->N;
+  const int es = d->prec == 0 ? 8 : 4, eg = d->prec == 0 ? 8 : (d->prec == 2 ? 2 : 4);
+  void *fa, *fb = nullptr;
+  int esz;
+  if (stage == 4 || stage == 6) {
+    fa = d->f[F_P0 + so];
+    fb = d->f[F_Q0 + so];
+    esz = es;
+  } else if (stage == 1 || stage == 2 || stage == 5) {
+    fa = d->f[stage == 2 ? F_G2 : F_G1];
+    if (stage == 5) fb = d->f[F_G2];
+    esz = eg;
+  } else {
+    return;
+  }
+  const bool state = stage == 4 || stage == 6;
+  const int pitch = state ? d->pitch_s : d->pitch_g;
+  const int64_t plane = state ? d->plane_s : d->plane_g;
+  const int hx = 16 / esz;
+  if (esz == 8) wrap_pair<unsigned long long>(fa, fb, N, pitch, plane, hx, tid, nth);
+  else if (esz == 4) wrap_pair<unsigned>(fa, fb, N, pitch, plane, hx, tid, nth);
+  else wrap_pair<unsigned short>(fa, fb, N, pitch, plane, hx, tid, nth);
+}
+
+bool stage_needs_wrap(int stage) { return stage == 1 || stage == 2 || stage >= 4; }
+
+cudaError_t launch_wrap(Desc *descs, const int *ndesc, int max_desc, int k, int stage,
+                        int blocks, cudaStream_t st) {
+  wrap_kernel<<<dim3(blocks, max_desc), 256, 0, st>>>(descs, ndesc, k, stage);
+  return cudaGetLastError();
+}
+
 // Host-requested changes to a running context, applied in stream order.
 __global__ void set_run_kernel(Desc *d, long long add_steps, double t0, double dt, double thr,
                                int reset) {

@@ -12,6 +12,12 @@ cudaError_t launch_unpack(int prec, const void *hi, const void *lo, double *dst,
 cudaError_t launch_bumps(int prec, void *hi, void *lo, int N, int pitch, int hx, int periodic,
                          double h, int nb, const double *d_prm, cudaStream_t st);
 cudaError_t launch_advance(Desc *descs, const int *ndesc, int max_desc, int K, cudaStream_t st);
+// Periodic ghost copies of the fields stage `stage` (1..6, 5 and 6 the fused
+// pairs) wrote for step k of the batch; contexts that are not periodic or did
+// not take the step are skipped.  `blocks` blocks of 256 threads per context.
+bool stage_needs_wrap(int stage);
+cudaError_t launch_wrap(Desc *descs, const int *ndesc, int max_desc, int k, int stage,
+                        int blocks, cudaStream_t st);
 cudaError_t launch_set_run(Desc *d, long long add_steps, double t0, double dt, double thr,
                            int reset, cudaStream_t st);
 cudaError_t launch_signpack(int prec, const void *hi, const void *lo, int N, int pitch, int hx,

@@ -8,10 +8,12 @@
 //       element (x, y, z) at  z*plane + (y + 2)*pitch + (x + HX),
 //       pitch = round_up(N + 2*HX, HX),  plane = (N + 4)*pitch.
 //   Zero-Dirichlet: ghosts stay 0 (the two ghost layers of Eq. BC, zeroed at
-//   allocation and never written).  Periodic: every writer also stores the
-//   wrapped copies x in {-2,-1,N,N+1} and y in {-2,-1,N,N+1}.  z-ghosts come
-//   from the TMA unit: out-of-range z planes read as zero (Dirichlet) or the
-//   plane index is wrapped (periodic).
+//   allocation and never written).  Periodic: the wrapped copies x in
+//   {-2,-1,N,N+1} and y in {-2,-1,N,N+1} are written by the initial-data
+//   kernels and, after each stage launch, by a ghost-copy launch for the
+//   fields later stages read with a halo (the stage kernels store interior
+//   points only).  z-ghosts come from the TMA unit: out-of-range z planes read
+//   as zero (Dirichlet) or the plane index is wrapped (periodic).
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>

@@ -201,6 +201,8 @@ extern "C" hbe_status hbe_step_fp64_noalloc(int N, double L, double mu, double l
       void *args[] = {&prm};
       NA_CK(cudaLaunchKernel(ks[s4].fn, dim3(grid[s4]), dim3(ks[s4].threads), args, ks[s4].smem,
                              st));
+      if (bc == 1 && stage_needs_wrap(s4 + 1))
+        NA_CK(launch_wrap(d_desc, d_counts + 1, 1, 0, s4 + 1, 2 * sms, st));
     }
     NA_CK(launch_advance(d_desc, d_counts + 1, 1, 1, st));
   }

@@ -220,50 +220,19 @@ __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
   e = (a - aa) + (b - bb);
 }
 
-// Store VEC values of a field at interior point (x, y) of a plane of the padded
-// layout (`row` points at the row's x = 0), and for periodic problems the ghost
-// rows beyond the y edges (`edge`).  `ragged`: the tile may cross x = N
-// (mask); `edge`: periodic tile touching a wrap band (write the ghost copies).
+// Store VEC values of a field at interior point x of a row of the padded
+// layout (`row` points at the row's x = 0) in a tile that crosses x = N: the
+// points at x >= N are skipped.  (Periodic ghost copies are written by a
+// separate launch after the stage, so the stage kernels store interior points
+// only.)
 template <class T, class TM, int VEC>
-__device__ __forceinline__ void store_point(T *row, int64_t pitch, int N, bool ragged, bool edge,
-                                            int x, int y, const TM (&v)[VEC]) {
-  if (!ragged || x + VEC <= N) {
+__device__ __forceinline__ void store_ragged(T *row, int N, int x, const TM (&v)[VEC]) {
+  if (x + VEC <= N) {
     store_as<T, TM, VEC>(row + x, v);
   } else {
 #pragma unroll
     for (int j = 0; j < VEC; ++j)
       if (x + j < N) row[x + j] = narrow<T>(v[j]);
-  }
-  if (edge) {
-#pragma unroll
-    for (int j = 0; j < VEC; ++j) {
-      const int xx = x + j;
-      if (xx >= N) continue;
-      const T val = narrow<T>(v[j]);
-      if (y < 2) row[(int64_t)N * pitch + xx] = val;
-      if (y >= N - 2) row[-(int64_t)N * pitch + xx] = val;
-    }
-  }
-}
-
-// Periodic x ghosts: columns N, N+1 copy x = 0, 1 and columns -2, -1 copy
-// x = N-2, N-1, written by the lanes that hold those points (`p` points at the
-// lane's first point).  `vec`: N is a multiple of VEC, so each such lane copies
-// its whole vector with one aligned store (the extra columns are the wrapped
-// values too); the store is predicated, so the warp does not branch.
-template <class T, class TM, int VEC>
-__device__ __forceinline__ void store_xghost(T *p, int N, int x, bool on, bool vec,
-                                             const TM (&v)[VEC]) {
-  if (vec) {
-    T *g = x < 2 ? p + N : p - N;
-    if (on) store_as<T, TM, VEC>(g, v);
-  } else if (on) {
-#pragma unroll
-    for (int j = 0; j < VEC; ++j) {
-      const int xx = x + j;
-      if (xx < 2) p[j + N] = narrow<T>(v[j]);
-      else if (xx >= N - 2 && xx < N) p[j - N] = narrow<T>(v[j]);
-    }
   }
 }
 
@@ -549,7 +518,7 @@ struct Consumer {
 
   struct Item {
     int N, x, z0, nplanes, set;
-    bool periodic, ragged, lane_edge, xok, xg_vec;
+    bool ragged, xok;
     int64_t pitch_s, plane_s, pitch_g, plane_g, row_s, row_g;
     int y0;
     TG *outG0, *outG1;
@@ -662,23 +631,15 @@ struct Consumer {
         }
       }
       const bool rok = it.xok && y < it.N;
-      const bool edge = it.periodic && (y < 2 || y >= it.N - 2);
-      const bool fast = rok && !it.ragged && !edge;
+      const bool fast = rok && !it.ragged;
       if constexpr (S <= 3 || S == 5) {
         const int64_t off = (int64_t)z * it.plane_g + it.row_g + r * it.pitch_g;
         if (fast) {
           store_as<TG, TM, VEC>(it.outG0 + off, res[0]);
           if constexpr (S == 5) store_as<TG, TM, VEC>(it.outG1 + off, res[KN - 1]);
         } else if (rok) {
-          store_point<TG, TM, VEC>(it.outG0 + off - it.x, it.pitch_g, it.N, it.ragged, edge, it.x, y, res[0]);
-          if constexpr (S == 5)
-            store_point<TG, TM, VEC>(it.outG1 + off - it.x, it.pitch_g, it.N, it.ragged, edge, it.x, y, res[KN - 1]);
-        }
-        if (it.periodic) {
-          const bool on = it.lane_edge && rok;
-          store_xghost<TG, TM, VEC>(it.outG0 + off, it.N, it.x, on, it.xg_vec, res[0]);
-          if constexpr (S == 5)
-            store_xghost<TG, TM, VEC>(it.outG1 + off, it.N, it.x, on, it.xg_vec, res[KN - 1]);
+          store_ragged<TG, TM, VEC>(it.outG0 + off - it.x, it.N, it.x, res[0]);
+          if constexpr (S == 5) store_ragged<TG, TM, VEC>(it.outG1 + off - it.x, it.N, it.x, res[KN - 1]);
         }
       } else {
         // RK4 combine (Sec. 2.1): p' = p + dt q + dt^2/6 (G1 + G2 + G3),
@@ -717,20 +678,11 @@ struct Consumer {
             store_as<TS, TM, VEC>(it.outQL + off, ql);
           }
         } else if (rok) {
-          store_point<TS, TM, VEC>(it.outP + off - it.x, it.pitch_s, it.N, it.ragged, edge, it.x, y, pn);
-          store_point<TS, TM, VEC>(it.outQ + off - it.x, it.pitch_s, it.N, it.ragged, edge, it.x, y, qn);
+          store_ragged<TS, TM, VEC>(it.outP + off - it.x, it.N, it.x, pn);
+          store_ragged<TS, TM, VEC>(it.outQ + off - it.x, it.N, it.x, qn);
           if constexpr (C::KAHAN) {
-            store_point<TS, TM, VEC>(it.outPL + off - it.x, it.pitch_s, it.N, it.ragged, edge, it.x, y, pl);
-            store_point<TS, TM, VEC>(it.outQL + off - it.x, it.pitch_s, it.N, it.ragged, edge, it.x, y, ql);
-          }
-        }
-        if (it.periodic) {
-          const bool on = it.lane_edge && rok;
-          store_xghost<TS, TM, VEC>(it.outP + off, it.N, it.x, on, it.xg_vec, pn);
-          store_xghost<TS, TM, VEC>(it.outQ + off, it.N, it.x, on, it.xg_vec, qn);
-          if constexpr (C::KAHAN) {
-            store_xghost<TS, TM, VEC>(it.outPL + off, it.N, it.x, on, it.xg_vec, pl);
-            store_xghost<TS, TM, VEC>(it.outQL + off, it.N, it.x, on, it.xg_vec, ql);
+            store_ragged<TS, TM, VEC>(it.outPL + off - it.x, it.N, it.x, pl);
+            store_ragged<TS, TM, VEC>(it.outQL + off - it.x, it.N, it.x, ql);
           }
         }
       }
@@ -764,7 +716,6 @@ struct Consumer {
       }
       Item it;
       it.N = d->N;
-      it.periodic = d->bc == 1;
       it.set = (int)(n & 1);
       const int so = it.set ^ 1;
       const int x0 = (w.y & 0xffff) * TX;
@@ -774,9 +725,6 @@ struct Consumer {
       it.ragged = x0 + TX > it.N;
       it.x = x0 + self.lx0;
       it.xok = it.x < it.N;
-      // periodic ghost copies are written only by the lanes / rows next to a wrap
-      it.lane_edge = it.periodic && (it.x < 2 || it.x + VEC > it.N - 2);
-      it.xg_vec = it.N % VEC == 0;
       it.pitch_s = d->pitch_s; it.plane_s = d->plane_s;
       it.pitch_g = d->pitch_g; it.plane_g = d->plane_g;
       it.row_s = (int64_t)(it.y0 + self.ly0 + 2) * it.pitch_s + HXS + it.x;
