@@ -243,6 +243,44 @@ def test_batch_alone_equals_mixed(hbe):
         assert np.array_equal(finished[rid], alone[rid]), rid
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_with_periodic_members_equals_alone(hbe, prec):
+    """Periodic and zero-Dirichlet members in one batch (ragged sizes, their
+    own step counts): the batched graph's ghost copies serve the periodic
+    members, and every member ends bit for bit where it ends alone."""
+    cases = [(24, 1, 7), (40, 0, 9), (36, 1, 12), (64, 1, 5), (20, 0, 11), (44, 1, 8)]
+    probs = [rand_problem(N, bc, seed=10 + i) for i, (N, bc, _) in enumerate(cases)]
+    alone = []
+    for prob, (_, _, n) in zip(probs, cases):
+        with hbe.Solver(prob.N, prob.L, prob.mu, prob.lam, prob.bc, prec) as s:
+            s.set_initial(prob.phi0, prob.phi1)
+            s.step(n, prob.dt)
+            alone.append(s.read()[:2])
+    b = hbe.Batch(prec, K=4)
+    solvers = []
+    for i, (prob, (_, _, n)) in enumerate(zip(probs, cases)):
+        s = hbe.Solver(prob.N, prob.L, prob.mu, prob.lam, prob.bc, prec)
+        s.set_initial(prob.phi0, prob.phi1)
+        solvers.append(s)
+        if i < 3:
+            b.add(s, n, prob.dt)
+    done = {}
+    later = list(range(3, len(cases)))
+    while len(b) or later:
+        for s in b.run():
+            done[solvers.index(s)] = s.read()[:2]
+        if later:  # joins while others are running
+            i = later.pop(0)
+            b.add(solvers[i], cases[i][2], probs[i].dt)
+    b.close()
+    for s in solvers:
+        s.close()
+    assert sorted(done) == list(range(len(cases)))
+    for i in range(len(cases)):
+        assert np.array_equal(done[i][0], alone[i][0]), i
+        assert np.array_equal(done[i][1], alone[i][1]), i
+
+
 def test_errors_are_returned_not_raised_by_the_library(hbe):
     with pytest.raises(hbe.HBEError):
         hbe.Solver(4, 1.0, 1.0, 1.0)
