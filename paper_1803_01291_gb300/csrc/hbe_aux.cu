@@ -430,10 +430,15 @@ __global__ void analysis_kernel(const T *__restrict__ phi, const T *__restrict__
   const int64_t n3 = (int64_t)N * N * N;
   double s1 = 0.0, s3 = 0.0, lmax = 0.0, sup = 0.0, bad = 0.0;
   auto at = [&](int x, int y, int z) -> double {
-    // padded layout: x and y ghosts are stored (0 or wrapped); z wraps or reads 0
-    if (z < 0 || z >= N) {
-      if (!periodic) return 0.0;
+    // outside the box: 0 (Dirichlet; the stored ghost layers are 0 too) or the
+    // wrapped node (periodic), indexed directly so that nothing depends on the
+    // ghost copies of the compensation parts
+    if (periodic) {
+      x = (x + N) % N;
+      y = (y + N) % N;
       z = (z + N) % N;
+    } else if (z < 0 || z >= N) {
+      return 0.0;
     }
     const int64_t o = (int64_t)z * plane + (int64_t)(y + 2) * pitch + x + hx;
     double v = (double)phi[o];

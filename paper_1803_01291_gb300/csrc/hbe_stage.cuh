@@ -17,7 +17,9 @@
 // Stage 4 writes the new state to the other buffer set (ping-pong), so no
 // field a stage reads with a halo is written by that stage.
 //
-// Kernel shape (one launch per stage, persistent blocks over a work list):
+// Kernel shape (one launch per stage or per fused pair of stages -- stages
+// 1+2 and stages 3+4 with the combine, which share the p, q tiles -- with
+// persistent blocks over a work list):
 //   * a block owns a TX x TY tile in x-y (TX = 32 VEC: one warp spans the row,
 //     each lane VEC consecutive x points) and marches along z over a chunk;
 //   * one producer warp streams every z-plane of every input field into a
@@ -32,6 +34,8 @@
 //     window.  When a warp is done with a slot it arrives on the slot's
 //     "empty" mbarrier; the producer refills a slot once all consumers have
 //     released it.  There is no block-wide synchronisation in the plane loop.
+//   * results are stored as interior points only; the periodic ghost copies
+//     are made by a separate launch after the stage (hbe_aux.cu).
 #pragma once
 #include <cuda_bf16.h>
 
@@ -412,8 +416,7 @@ __device__ __forceinline__ TM lap_g(TM c43, TM cm12, TM ccen, TM nlam, TM m3, bo
 
 // One consumer warp.  Kinds (KN = 1 for one stage, 2 for a fused pair) share
 // the ring tiles; the register window holds P of every kind at planes
-// z-2..z+2 for the warp's own points, indexed by plane number mod 5 so that the
-// unrolled plane loop never moves registers.
+// z-2..z+2 for the warp's own points and is shifted by one plane per step.
 template <class C>
 struct Consumer {
   using TS = typename C::TS;

@@ -59,3 +59,27 @@ def test_homogeneous_integral_is_volume_times_value(hbe):
     # the FD4 weights sum to zero; on a constant only rounding of the weighted
     # terms (a few ulp of 15/h^2 * 0.7) is left
     assert a["laplacian_monitor"] <= 1e-13
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_periodic_monitor_at_the_wrap(hbe, prec):
+    """Periodic data whose largest Laplacian sits on the x = 0 face: after a few
+    steps (compensated state with nonzero low parts) the monitor still equals
+    its definition on the read field, so the wrap across the faces uses the
+    current values."""
+    N, L, mu, lam = 32, 10.0, 1.3, 0.7
+    xs = hi.grid_coords(N, L, 1) + L / 2  # node 0 at 0: the x = 0 face
+    k = 2 * math.pi / L
+    # cos(k x) + 0.3 cos(2 k x): |phi_xx| peaks only at node 0, next to the wrap
+    fx = np.cos(k * xs) + 0.3 * np.cos(2 * k * xs)
+    phi0 = (fx[None, None, :] + 0.2 * np.sin(k * xs)[None, :, None]
+            + 0.1 * np.cos(k * xs)[:, None, None]) * np.ones((N, N, N))
+    phi1 = 0.3 * np.roll(phi0, 5, axis=2)
+    h = hi.grid_spacing(N, L, 1)
+    with hbe.Solver(N, L, mu, lam, 1, prec) as s:
+        s.set_initial(phi0, phi1)
+        s.step(7, h / 4)
+        phi, psi, t = s.read()
+        a = s.analysis()
+    lap = oracle.laplacian(phi, h, 1)
+    assert math.isclose(a["laplacian_monitor"], math.exp(-2 * t) * np.max(np.abs(lap)), rel_tol=1e-12)
