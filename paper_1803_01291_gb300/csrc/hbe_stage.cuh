@@ -38,6 +38,7 @@
 //     are made by a separate launch after the stage (hbe_aux.cu).
 #pragma once
 #include <cuda_bf16.h>
+#include <type_traits>
 
 
 #include "hbe_common.cuh"
@@ -49,21 +50,28 @@ struct PrecFP64 {
   using TS = double; using TG = double; using TM = double;
   static constexpr bool KAHAN = false;
   static constexpr bool DIFF = false;   // merged-centre stencil (fewest FP64 ops)
+  // plane loop unrolled 5 times over a rotating register window (no register
+  // moves) where that measured faster than shifting the window: FP32 with
+  // compensated state only (FP64 spills with it, BF16 / plain FP32 gain nothing)
+  static constexpr bool ROTATE = false;
 };
 struct PrecFP32 {
   using TS = float; using TG = float; using TM = float;
   static constexpr bool KAHAN = true;
   static constexpr bool DIFF = true;    // neighbour-minus-centre stencil (less cancellation)
+  static constexpr bool ROTATE = true;
 };
 struct PrecBF16 {
   using TS = float; using TG = __nv_bfloat16; using TM = float;
   static constexpr bool KAHAN = true;
   static constexpr bool DIFF = true;
+  static constexpr bool ROTATE = false;
 };
 struct PrecFP32Plain {
   using TS = float; using TG = float; using TM = float;
   static constexpr bool KAHAN = false;
   static constexpr bool DIFF = true;
+  static constexpr bool ROTATE = false;
 };
 
 __host__ __device__ constexpr int align128(int b) { return (b + 127) & ~127; }
@@ -113,6 +121,7 @@ struct StageCfg {
   static constexpr int SMEM = HEADER + RING * SLOT_BYTES;
   static_assert(SMEM <= 227 * 1024, "ring of 4 slots does not fit in 227 KB of shared memory");
   static constexpr int MINB = MINB_;  // blocks per SM the registers must allow
+  static constexpr bool ROTATE = PR::ROTATE;
   static_assert(VEC == 1 || VEC == 2 || VEC == 4, "1, 2 or 4 x points per lane");
   static_assert(VEC * (int)sizeof(TM) <= 16, "lane vector of <= 16 bytes");
   static_assert(HXS >= 2 && HXG >= 2 && HXS % VEC == 0 && HXG % VEC == 0, "halo alignment");
@@ -416,7 +425,7 @@ __device__ __forceinline__ TM lap_g(TM c43, TM cm12, TM ccen, TM nlam, TM m3, bo
 
 // One consumer warp.  Kinds (KN = 1 for one stage, 2 for a fused pair) share
 // the ring tiles; the register window holds P of every kind at planes
-// z-2..z+2 for the warp's own points and is shifted by one plane per step.
+// z-2..z+2 for the warp's own points (rotating or shifted, see plane()).
 template <class C>
 struct Consumer {
   using TS = typename C::TS;
@@ -530,19 +539,26 @@ struct Consumer {
 
   // One z-plane: plane m of the item enters the window (slot `slot`); for
   // m >= 4 the output plane m - 4 (loaded as plane m - 2, slot s2) is computed.
-  // The window is shifted by one plane first; the newest plane is at index 4.
+  // ROT >= 0: plane j lives at window index j mod 5 and m mod 5 == ROT (the
+  // plane loop is unrolled 5 times, so no register moves); ROT < 0: the window
+  // is shifted by one plane first and the newest plane is at index 4.
+  template <int ROT>
   __device__ __forceinline__ void plane(const Item &it, int m, int slot, int s2,
                                         TM (&win)[5][KN][VY][VEC], TM &run_max,
                                         bool &bad) const {
-    constexpr int W0 = 4, WM1 = 3, WM2 = 2, WM3 = 1, WM4 = 0;
+    constexpr int R0 = ROT < 0 ? 4 : ROT;
+    constexpr int W0 = R0 % 5, WM1 = (R0 + 4) % 5, WM2 = (R0 + 3) % 5, WM3 = (R0 + 2) % 5,
+                  WM4 = (R0 + 1) % 5;
+    if constexpr (ROT < 0) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int kk = 0; kk < KN; ++kk)
+        for (int kk = 0; kk < KN; ++kk)
 #pragma unroll
-        for (int r = 0; r < VY; ++r)
+          for (int r = 0; r < VY; ++r)
 #pragma unroll
-          for (int j = 0; j < VEC; ++j) win[a][kk][r][j] = win[a + 1][kk][r][j];
+            for (int j = 0; j < VEC; ++j) win[a][kk][r][j] = win[a + 1][kk][r][j];
+    }
     const unsigned char *base = ring + slot * C::SLOT_BYTES;
 #pragma unroll
     for (int r = 0; r < VY; ++r) {
@@ -759,7 +775,7 @@ struct Consumer {
       TM run_max = (TM)0;
       bool bad = false;
       // one plane: wait for its slot, compute, release what is no longer needed
-      auto step = [&](int m) -> bool {
+      auto step = [&](auto rot, int m) -> bool {
         if (!mbar_wait_bounded(&full[slot], phase)) {
           *abort_flag = 1;
           atomicOr(prm.err, (unsigned)DEV_ERR_TIMEOUT);
@@ -767,7 +783,7 @@ struct Consumer {
         }
         if (*abort_flag) return false;
         const int s2 = slot >= 2 ? slot - 2 : slot + RING - 2;  // slot of plane m - 2
-        self.plane(it, m, slot, s2, win, run_max, bad);
+        self.template plane<decltype(rot)::value>(it, m, slot, s2, win, run_max, bad);
         __syncwarp();
         if (self.lane == 0) {
           if (m < 2 || m >= it.nplanes - 2) mbar_arrive(&empty[slot]);
@@ -777,7 +793,23 @@ struct Consumer {
         return true;
       };
       bool ok = true;
-      for (int m = 0; ok && m < it.nplanes; ++m) ok = step(m);
+      using I0 = std::integral_constant<int, 0>;
+      using I1 = std::integral_constant<int, 1>;
+      using I2 = std::integral_constant<int, 2>;
+      using I3 = std::integral_constant<int, 3>;
+      using I4 = std::integral_constant<int, 4>;
+      int m = 0;
+      if constexpr (C::ROTATE) {
+        for (; ok && m + 5 <= it.nplanes; m += 5)
+          ok = step(I0{}, m) && step(I1{}, m + 1) && step(I2{}, m + 2) && step(I3{}, m + 3) &&
+               step(I4{}, m + 4);
+        if (ok && m < it.nplanes) ok = step(I0{}, m++);
+        if (ok && m < it.nplanes) ok = step(I1{}, m++);
+        if (ok && m < it.nplanes) ok = step(I2{}, m++);
+        if (ok && m < it.nplanes) ok = step(I3{}, m++);
+      } else {
+        for (; ok && m < it.nplanes; ++m) ok = step(std::integral_constant<int, -1>{}, m);
+      }
       if (!ok) return;
       if constexpr (S == 4 || S == 6) {
         double v = (double)run_max;
