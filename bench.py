@@ -346,7 +346,7 @@ def radial_leg(hbe, torch, cpu: bool = True):
     node-steps per second over one launch that integrates every problem, timed
     with CUDA events; the FP32 roofline is the FP32 FMA rate of the SMs, the
     FP64 one the measured FP64 FMA rate.  CPU: the radial oracle (FP64 numpy)
-    on one problem for 2000 steps."""
+    on one problem for 20000 steps."""
     from paper_1803_01291_gb300 import radial
     w = radial_workload()
     B, n = w["phi0"].shape
@@ -378,11 +378,11 @@ def radial_leg(hbe, torch, cpu: bool = True):
     if cpu:
         import oracle.radial_phi as rp
         t0 = time.perf_counter()
-        rp.run(w["phi0"][0], w["phi1"][0], w["R"], w["mu"][0], w["lam"][0], 0.0, w["dt"], 2000)
+        rp.run(w["phi0"][0], w["phi1"][0], w["R"], w["mu"][0], w["lam"][0], 0.0, w["dt"], 20000)
         secs = time.perf_counter() - t0
-        out["cpu_baseline"] = {"value": n * 2000 / secs / 1e9, "unit": "Gnode-steps/s",
+        out["cpu_baseline"] = {"value": n * 20000 / secs / 1e9, "unit": "Gnode-steps/s",
                                "cores": 1, "kind": "oracle",
-                               "sample": f"one problem of the sweep, 2000 steps (FP64 numpy, one "
+                               "sample": f"one problem of the sweep, 20000 steps (FP64 numpy, one "
                                          f"core), {secs:.2f} s"}
     return out
 
@@ -566,7 +566,7 @@ def main():
         line["radial"] = radial_leg(hbe, torch, cpu=(rank == 0 and not args.no_cpu))
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(prob, 2)
+        line["cpu_baseline"] = cpu_baseline(prob, 6 if N >= 512 else 2)
 
     if rank == 0:
         print(json.dumps(line), flush=True)
