@@ -23,7 +23,7 @@ from typing import Callable, Dict, List, Optional, Sequence
 import numpy as np
 
 from . import _lib
-from .solver import Batch, Solver, workspace_bytes
+from .solver import Batch, Solver, variants, workspace_bytes
 
 
 @dataclass
@@ -113,11 +113,25 @@ class Server:
         self.keep_fields = keep_fields
         self.tuning = tuning
         self.batch = Batch(prec, K)
+        self._small_variant = None
         self.in_use = 0
         self._live: Dict[int, tuple] = {}
 
     def need_bytes(self, req: SolveRequest) -> int:
         return workspace_bytes(req.N, req.bc, self.prec)
+
+    def _default_variant(self, N: int) -> int:
+        """Tile variant for a member of size N when no tuning is given: below
+        256^3 the variant with the smallest tile (less of each tile wasted past
+        the grid edge, more tiles to spread over the SMs; 1.1-2x faster alone on
+        32^3..192^3 grids), else variant 0."""
+        if N >= 256:
+            return 0
+        if self._small_variant is None:
+            vs = variants(self.prec)
+            self._small_variant = min(range(len(vs)),
+                                      key=lambda i: vs[i]["tile_x"] * vs[i]["tile_y"])
+        return self._small_variant
 
     def _admit(self, req: SolveRequest, now: float):
         torch = self.torch
@@ -125,6 +139,8 @@ class Server:
         if self.tuning is not None:
             v, zc = self.tuning(req.N, self.prec)
             s.set_tuning(v, zc)
+        else:
+            s.set_tuning(self._default_variant(req.N), 0)
         if req.bumps is not None:
             s.set_initial_bumps(req.bumps)
         else:
