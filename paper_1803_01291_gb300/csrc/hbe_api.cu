@@ -2,11 +2,13 @@
 // TMA descriptors, work lists, CUDA-graph stepping, diagnostics, checkpoints
 // and the batched (continuous-batching) runner.
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <set>
@@ -281,6 +283,20 @@ hbe_status launch_stage(std::string &err, const KernelInfo &ki, int grid, const 
   return HBE_OK;
 }
 
+// Debug mode: periodic contexts start with NaN bit patterns in every field
+// (HBE_DEBUG_NAN_GHOSTS set and not "0"), read at each context creation.
+bool nan_canary(const hbe_ctx *ctx) {
+  if (ctx->bc != HBE_BC_PERIODIC) return false;
+  const char *v = std::getenv("HBE_DEBUG_NAN_GHOSTS");
+  return v && *v && std::strcmp(v, "0") != 0;
+}
+
+// NVTX range over a host call (visible in Nsight timelines; no cost without a tool)
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+
 // kernels one RK4 step launches: the stage kernels, and for a periodic context
 // the ghost copy after each stage whose output is read with a halo
 int launches_per_step(const hbe_ctx *ctx) {
@@ -444,7 +460,11 @@ hbe_status create_common(int N, double L, double mu, double lambda, int bc, int 
       return bail(e_ == cudaErrorMemoryAllocation ? HBE_ENOMEM : HBE_ECUDA);        \
     }                                                                               \
   } while (0)
-  CKB(cudaMemset(ctx->ws, 0, ctx->ws_bytes));
+  // zero: the Dirichlet ghost layers (never written again).  A periodic context
+  // under HBE_DEBUG_NAN_GHOSTS starts from all-ones bit patterns instead (NaN in
+  // every precision), so that any ghost cell a stage reads before the ghost copy
+  // has refreshed it turns the result non-finite.
+  CKB(cudaMemset(ctx->ws, nan_canary(ctx) ? 0xFF : 0, ctx->ws_bytes));
   CKB(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
   CKB(cudaMalloc(&ctx->d_tmaps, NUM_TMAPS * sizeof(CUtensorMap)));
   CKB(cudaMalloc(&ctx->d_maxabs, kMaxK * sizeof(unsigned long long)));
@@ -648,11 +668,13 @@ static hbe_status set_initial_impl(hbe_ctx *ctx, const double *phi0, const doubl
 }
 
 hbe_status hbe_set_initial(hbe_ctx *ctx, const double *phi0, const double *phi1, double t0) {
+  Range range_("hbe_set_initial");
   return set_initial_impl(ctx, phi0, phi1, t0, false);
 }
 
 hbe_status hbe_set_initial_device(hbe_ctx *ctx, const double *d_phi0, const double *d_phi1,
                                   double t0) {
+  Range range_("hbe_set_initial_device");
   hbe_status st = set_initial_impl(ctx, d_phi0, d_phi1, t0, true);
   if (st == HBE_OK && ctx) {
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -664,6 +686,7 @@ hbe_status hbe_set_initial_device(hbe_ctx *ctx, const double *d_phi0, const doub
 hbe_status hbe_set_initial_bumps(hbe_ctx *ctx, int n0, const double *A0, const double *R0,
                                  const double *c0, int n1, const double *A1, const double *R1,
                                  const double *c1, double t0) {
+  Range range_("hbe_set_initial_bumps");
   if (!ctx) return HBE_EINVAL;
   if (ctx->in_batch) return set_err(ctx->err, HBE_ESTATE, "context is in a batch");
   if (n0 < 0 || n1 < 0 || n0 > 64 || n1 > 64)
@@ -696,7 +719,7 @@ hbe_status hbe_set_initial_bumps(hbe_ctx *ctx, int n0, const double *A0, const d
                   ctx->hxs, ctx->bc, ctx->h, n1, d_prm + 64 * 5, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   // the stage kernels overwrite G before reading it, but the Dirichlet ghosts must be 0
-  CK(cudaMemset(ctx->f[F_G1], 0, 3 * ctx->bytes_g));
+  CK(cudaMemset(ctx->f[F_G1], nan_canary(ctx) ? 0xFF : 0, 3 * ctx->bytes_g));
   Desc &d = *ctx->h_desc;
   d.t0 = t0;
   d.dt = 0.0;
@@ -724,6 +747,7 @@ hbe_status hbe_set_stop(hbe_ctx *ctx, double threshold) {
 }
 
 hbe_status hbe_step_async(hbe_ctx *ctx, int64_t nsteps, double dt) {
+  Range range_("hbe_step");
   if (!ctx) return HBE_EINVAL;
   if (ctx->in_batch) return set_err(ctx->err, HBE_ESTATE, "context is in a batch");
   if (!ctx->has_state) return set_err(ctx->err, HBE_ESTATE, "no initial data");
@@ -758,6 +782,7 @@ hbe_status hbe_step_async(hbe_ctx *ctx, int64_t nsteps, double dt) {
 }
 
 hbe_status hbe_sync(hbe_ctx *ctx) {
+  Range range_("hbe_sync");
   if (!ctx) return HBE_EINVAL;
   const bool was_pending = ctx->pending;
   hbe_status st = sync_ctx(ctx);
@@ -780,6 +805,7 @@ hbe_status hbe_step(hbe_ctx *ctx, int64_t nsteps, double dt) {
 }
 
 hbe_status hbe_profile_stages(hbe_ctx *ctx, int64_t nsteps, double dt, float *ms_per_stage) {
+  Range range_("hbe_profile_stages");
   if (!ctx || !ms_per_stage) return HBE_EINVAL;
   if (ctx->in_batch) return set_err(ctx->err, HBE_ESTATE, "context is in a batch");
   if (!ctx->has_state) return set_err(ctx->err, HBE_ESTATE, "no initial data");
@@ -885,6 +911,7 @@ static hbe_status read_impl(hbe_ctx *ctx, double *phi, double *psi, bool device)
 }
 
 hbe_status hbe_read(hbe_ctx *ctx, double *phi, double *psi, double *t) {
+  Range range_("hbe_read");
   if (!ctx) return HBE_EINVAL;
   if (!ctx->has_state) return set_err(ctx->err, HBE_ESTATE, "no initial data");
   hbe_status st = sync_ctx(ctx);
@@ -895,6 +922,7 @@ hbe_status hbe_read(hbe_ctx *ctx, double *phi, double *psi, double *t) {
 }
 
 hbe_status hbe_read_device(hbe_ctx *ctx, double *d_phi, double *d_psi) {
+  Range range_("hbe_read_device");
   if (!ctx) return HBE_EINVAL;
   if (!ctx->has_state) return set_err(ctx->err, HBE_ESTATE, "no initial data");
   hbe_status st = sync_ctx(ctx);
@@ -904,6 +932,7 @@ hbe_status hbe_read_device(hbe_ctx *ctx, double *d_phi, double *d_psi) {
 
 hbe_status hbe_diag(hbe_ctx *ctx, double eps, hbe_diag_t *out, uint32_t *pos_mask,
                     uint32_t *neg_mask) {
+  Range range_("hbe_diag");
   if (!ctx || !out) return HBE_EINVAL;
   if (!ctx->has_state) return set_err(ctx->err, HBE_ESTATE, "no initial data");
   if (!(eps >= 0.0)) return set_err(ctx->err, HBE_EINVAL, "eps must be >= 0");
@@ -952,6 +981,7 @@ hbe_status hbe_diag(hbe_ctx *ctx, double eps, hbe_diag_t *out, uint32_t *pos_mas
 }
 
 hbe_status hbe_analysis(hbe_ctx *ctx, double eps, hbe_analysis_t *out) {
+  Range range_("hbe_analysis");
   if (!ctx || !out) return HBE_EINVAL;
   if (!ctx->has_state) return set_err(ctx->err, HBE_ESTATE, "no initial data");
   if (!(eps >= 0.0)) return set_err(ctx->err, HBE_EINVAL, "eps must be >= 0");
@@ -1233,6 +1263,7 @@ static hbe_status batch_rebuild(hbe_batch *b) {
 }
 
 hbe_status hbe_batch_run(hbe_batch *b, hbe_ctx **finished, int max_finished, int *n_finished) {
+  Range range_("hbe_batch_run");
   if (!b || !n_finished) return HBE_EINVAL;
   *n_finished = 0;
   if (b->members.empty()) return HBE_OK;

@@ -281,6 +281,29 @@ def test_batch_with_periodic_members_equals_alone(hbe, prec):
         assert np.array_equal(done[i][1], alone[i][1]), i
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("prec", PRECS)
+def test_periodic_ghosts_under_nan_canary(hbe, prec, schedule, monkeypatch):
+    """With HBE_DEBUG_NAN_GHOSTS every field of a periodic context starts as NaN,
+    so a ghost cell read before the ghost-copy launch refreshed it would make
+    the result non-finite.  Ragged sizes, both schedules, several steps: the
+    result stays finite and within tolerance of the oracle."""
+    monkeypatch.setenv("HBE_DEBUG_NAN_GHOSTS", "1")
+    for N in (20, 36):
+        prob = rand_problem(N, 1, seed=N)
+        nsteps = 4
+        ref, _, _ = oracle.run(prob.phi0, prob.phi1, prob.L, prob.mu, prob.lam, 1, 0.0, prob.dt,
+                               nsteps)
+        with hbe.Solver(prob.N, prob.L, prob.mu, prob.lam, 1, prec) as s:
+            s.set_schedule(schedule)
+            s.set_initial(prob.phi0, prob.phi1)
+            st = s.step(nsteps, prob.dt)
+            phi, psi, _ = s.read()
+        assert st == hbe.OK
+        assert np.all(np.isfinite(phi)) and np.all(np.isfinite(psi))
+        assert relerr(phi, ref) <= TOL[prec]
+
+
 def test_errors_are_returned_not_raised_by_the_library(hbe):
     with pytest.raises(hbe.HBEError):
         hbe.Solver(4, 1.0, 1.0, 1.0)
