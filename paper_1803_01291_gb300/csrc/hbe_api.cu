@@ -408,6 +408,24 @@ size_t workspace_bytes(int N, int prec) {
   return nstate * bs + 3 * bg;
 }
 
+// Host-side fault injection for tests: HBE_FAULT="alloc:k" makes the k-th
+// context creation, counted from when the variable took its current value,
+// fail with HBE_ENOMEM as if the device were out of memory.
+bool injected_alloc_failure() {
+  static std::mutex mu;
+  static std::string last;
+  static long count = 0;
+  const char *v = std::getenv("HBE_FAULT");
+  const std::string cur = v ? v : "";
+  std::lock_guard<std::mutex> lock(mu);
+  if (cur != last) {
+    last = cur;
+    count = 0;
+  }
+  if (cur.compare(0, 6, "alloc:") != 0) return false;
+  return ++count == std::atol(cur.c_str() + 6);
+}
+
 hbe_status create_common(int N, double L, double mu, double lambda, int bc, int prec, void *ws,
                          size_t bytes, hbe_ctx **out) {
   if (!out) return HBE_EINVAL;
@@ -420,6 +438,7 @@ hbe_status create_common(int N, double L, double mu, double lambda, int bc, int 
     return s;
   };
   if (st != HBE_OK) return bail(st);
+  if (injected_alloc_failure()) return bail(HBE_ENOMEM);
   ctx->N = N; ctx->L = L; ctx->mu = mu; ctx->lambda = lambda; ctx->bc = bc; ctx->prec = prec;
   ctx->h = bc == HBE_BC_PERIODIC ? L / N : L / (N + 1);
   if (cudaGetDevice(&ctx->device) != cudaSuccess ||

@@ -80,6 +80,7 @@ class ServeStats:
     peak_members: int = 0
     peak_bytes: int = 0
     launches: int = 0
+    admission_retries: int = 0
 
     def summary(self) -> dict:
         lat = np.array([r.latency for r in self.results]) if self.results else np.zeros(1)
@@ -90,7 +91,8 @@ class ServeStats:
                 "makespan_s": self.makespan,
                 "gpoint_steps_per_s": self.work / self.makespan / 1e9 if self.makespan else 0.0,
                 "batch_runs": self.runs, "peak_members": self.peak_members,
-                "peak_state_bytes": self.peak_bytes, "gpu_launches": self.launches}
+                "peak_state_bytes": self.peak_bytes, "gpu_launches": self.launches,
+                "admission_retries": self.admission_retries}
 
 
 class Server:
@@ -133,6 +135,11 @@ class Server:
                                       key=lambda i: vs[i]["tile_x"] * vs[i]["tile_y"])
         return self._small_variant
 
+    def _out_of_memory(self, e: Exception) -> bool:
+        if isinstance(e, _lib.HBEError):
+            return e.status == _lib.ENOMEM
+        return isinstance(e, getattr(self.torch.cuda, "OutOfMemoryError", ()))
+
     def _admit(self, req: SolveRequest, now: float):
         torch = self.torch
         s = Solver(req.N, req.L, req.mu, req.lam, req.bc, self.prec)
@@ -174,7 +181,13 @@ class Server:
                 nb = self.need_bytes(r)
                 if self.in_use + nb > self.budget or len(self.batch) >= self.max_members:
                     break
-                self._admit(r, now)
+                try:
+                    self._admit(r, now)
+                except Exception as e:  # out of device memory: wait for a member to leave
+                    if not self._out_of_memory(e) or not len(self.batch):
+                        raise
+                    stats.admission_retries += 1
+                    break
                 stats.work += r.work
                 i += 1
             stats.peak_members = max(stats.peak_members, len(self.batch))

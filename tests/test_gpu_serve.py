@@ -68,3 +68,25 @@ def test_alone_baseline_runs(hbe):
     reqs = serve.requests_from_stream(small_stream(3, 9))
     out = serve.run_alone(reqs, hbe.FP64)
     assert out["requests"] == 3 and out["gpoint_steps_per_s"] > 0
+
+
+def test_server_requeues_after_allocation_failure(hbe, monkeypatch):
+    """Failure detection, injected on the host: the third context creation
+    fails with HBE_ENOMEM (HBE_FAULT=alloc:3).  The server keeps the request,
+    runs the batch it has, admits it later, and every result is still the
+    problem's result alone."""
+    from paper_1803_01291_gb300 import serve
+    reqs = serve.requests_from_stream(small_stream(6, 11))
+    monkeypatch.setenv("HBE_FAULT", "alloc:3")
+    srv = serve.Server(hbe.FP32, K=4)
+    stats = srv.run(reqs, realtime=False)
+    srv.close()
+    monkeypatch.delenv("HBE_FAULT")
+    assert stats.admission_retries == 1
+    assert sorted(r.rid for r in stats.results) == sorted(q.rid for q in reqs)
+    by_id = {r.rid: r for r in stats.results}
+    for q in reqs:
+        with hbe.Solver(q.N, q.L, q.mu, q.lam, 0, hbe.FP32) as s:
+            s.set_initial_bumps(q.bumps)
+            s.step(q.nsteps, q.dt)
+            assert s.diag()["max_abs_phi"] == by_id[q.rid].max_abs_phi
