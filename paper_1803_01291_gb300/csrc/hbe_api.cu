@@ -297,6 +297,13 @@ struct Range {
   ~Range() { nvtxRangePop(); }
 };
 
+// blocks of the ghost-copy launch of one context: a thread per row of a plane
+// (N^2 rows; more threads in flight hide the latency of the scattered accesses)
+int wrap_blocks(const hbe_ctx *ctx) {
+  const long long rows = (long long)ctx->N * ctx->N;
+  return (int)std::min<long long>(4096, std::max<long long>(2 * ctx->sms, (rows + 255) / 256));
+}
+
 // kernels one RK4 step launches: the stage kernels, and for a periodic context
 // the ghost copy after each stage whose output is read with a halo
 int launches_per_step(const hbe_ctx *ctx) {
@@ -319,7 +326,7 @@ hbe_status ensure_graph(hbe_ctx *ctx) {
       StageParams p{ctx->d_desc, ctx->d_items, ctx->d_nitems, ctx->d_err, k};
       st = launch_stage(ctx->err, vt.k[ctx->variant][s], ctx->grid[s], p, ctx->cap_stream);
       if (st == HBE_OK && ctx->bc == HBE_BC_PERIODIC && stage_needs_wrap(s + 1)) {
-        cudaError_t ew = launch_wrap(ctx->d_desc, ctx->d_one, 1, k, s + 1, 2 * ctx->sms,
+        cudaError_t ew = launch_wrap(ctx->d_desc, ctx->d_one, 1, k, s + 1, wrap_blocks(ctx),
                                      ctx->cap_stream);
         if (ew != cudaSuccess) st = set_err(ctx->err, HBE_ECUDA, "%s", cudaGetErrorString(ew));
       }
@@ -855,7 +862,7 @@ hbe_status hbe_profile_stages(hbe_ctx *ctx, int64_t nsteps, double dt, float *ms
                         ctx->stream);
       CK(cudaEventRecord(ev[(n * nl + s) * 2 + 1], ctx->stream));
       if (st == HBE_OK && ctx->bc == HBE_BC_PERIODIC && stage_needs_wrap(first + s + 1)) {
-        CK(launch_wrap(ctx->d_desc, ctx->d_one, 1, 0, first + s + 1, 2 * ctx->sms, ctx->stream));
+        CK(launch_wrap(ctx->d_desc, ctx->d_one, 1, 0, first + s + 1, wrap_blocks(ctx), ctx->stream));
         ++wraps;
       }
     }

@@ -182,18 +182,35 @@ cudaError_t launch_advance(Desc *descs, const int *ndesc, int max_desc, int K, c
 // fields: stage 1 -> G1, stage 2 -> G2, stages 4 and 6 -> phi, psi of the new
 // state, stage 5 (stages 1 + 2) -> G1, G2; G3 and the compensation parts are
 // read at the point only.  Elements are moved as raw bits.
+template <class E> struct Pair;
+template <> struct Pair<unsigned long long> { using type = ulonglong2; };
+template <> struct Pair<unsigned> { using type = uint2; };
+template <> struct Pair<unsigned short> { using type = unsigned; };
+
 template <class E>
 __device__ void wrap_field(E *f, int N, int pitch, int64_t plane, int hx, long long tid,
                            long long nth) {
   const long long nx = (long long)N * N;
-  for (long long u = tid; u < nx; u += nth) {
-    const int z = (int)(u / N), y = (int)(u % N);
-    E *row = f + (int64_t)z * plane + (int64_t)(y + 2) * pitch + hx;
-    const E a = row[0], b = row[1], c = row[N - 2], d = row[N - 1];
-    row[-2] = c;
-    row[-1] = d;
-    row[N] = a;
-    row[N + 1] = b;
+  if ((N & 1) == 0) {
+    // columns 0,1 / N-2,N-1 / -2,-1 / N,N+1 are aligned pairs when N is even
+    using P = typename Pair<E>::type;
+    for (long long u = tid; u < nx; u += nth) {
+      const int z = (int)(u / N), y = (int)(u % N);
+      E *row = f + (int64_t)z * plane + (int64_t)(y + 2) * pitch + hx;
+      const P lo = *reinterpret_cast<const P *>(row), hi = *reinterpret_cast<const P *>(row + N - 2);
+      *reinterpret_cast<P *>(row - 2) = hi;
+      *reinterpret_cast<P *>(row + N) = lo;
+    }
+  } else {
+    for (long long u = tid; u < nx; u += nth) {
+      const int z = (int)(u / N), y = (int)(u % N);
+      E *row = f + (int64_t)z * plane + (int64_t)(y + 2) * pitch + hx;
+      const E a = row[0], b = row[1], c = row[N - 2], d = row[N - 1];
+      row[-2] = c;
+      row[-1] = d;
+      row[N] = a;
+      row[N + 1] = b;
+    }
   }
   // padded rows 0, 1 <- N, N+1 (y = N-2, N-1) and N+2, N+3 <- 2, 3 (y = 0, 1)
   const long long ny = (long long)N * 4 * N;
