@@ -55,6 +55,14 @@ def test_host_only_calls(lib):
         assert v.threads == 32 * (v.consumer_warps + 1)
         assert all(s <= 227 * 1024 for s in v.smem_bytes) and all(r >= 4 for r in v.ring)
         assert lib.hbe_variant_info(prec, n, ctypes.byref(v)) == _lib.EINVAL
+    # the radial solver's limits and argument checks run on the host
+    assert lib.hbe_radial_max_n(0) == lib.hbe_radial_max_n(1) == 4096
+    assert lib.hbe_radial_max_n(2) == 0
+    nul = None
+    assert lib.hbe_radial_run(1, 3, 1.0, nul, nul, nul, nul, 0.0, 0.01, 1, 0, 0, 0.0, 0.0,
+                              nul, nul, nul, nul, nul, nul) == _lib.EINVAL
+    assert lib.hbe_radial_run(1, 64, 1.0, nul, nul, nul, nul, 0.0, 0.01, 1, 0, 0, 0.0, 0.0,
+                              nul, nul, nul, nul, nul, nul) == _lib.EINVAL  # null arrays
 
 
 def test_product_never_imports_the_oracle():
