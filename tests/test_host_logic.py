@@ -1,0 +1,201 @@
+"""Host-side logic that needs no GPU: the bench's byte model and aggregation,
+the autotuner's selection and cache, the server's admission (memory budget,
+FIFO order, requeue after an allocation failure) with stand-ins for the
+device objects, and the seeded request stream."""
+import ctypes
+import json
+import math
+
+import numpy as np
+import pytest
+
+import __graft_entry__  # noqa: F401
+import bench
+import hbe_inputs as hi
+from paper_1803_01291_gb300 import _lib
+
+
+# ---------------------------------------------------------------- bench byte model
+def test_stage_bytes_match_the_design_table():
+    one = {"fp64": 80, "fp32": 56, "bf16": 48, "fp32_plain": 40}
+    zero = {"fp64": 152, "fp32": 92, "bf16": 74, "fp32_plain": 76}
+    for prec in one:
+        assert sum(bench.stage_bytes(prec, 1)) == one[prec]
+        assert sum(bench.stage_bytes(prec, 0)) == zero[prec]
+    assert bench.stage_bytes("fp32", 1) == [16, 40]
+
+
+def test_aggregate_is_all_units_over_the_slowest_rank():
+    assert bench.aggregate(2e9, 0.5, 4) == pytest.approx(16.0)
+
+
+# ---------------------------------------------------------------- autotuner
+def test_autotune_picks_the_fastest_and_caches_it(tmp_path, monkeypatch):
+    from paper_1803_01291_gb300 import autotune
+    monkeypatch.setenv("HBE_AUTOTUNE_CACHE", str(tmp_path / "c.json"))
+    monkeypatch.setattr(autotune, "_gpu_name", lambda: "test-gpu")
+    nvar = len(autotune.variants(_lib.FP32))
+
+    def fake(N, bc, prec, v, zc, steps=10, warmup=3, seed=0, schedule=1):
+        # fastest: schedule 0, variant nvar - 1, the second z-chunk candidate
+        zcs = list(autotune.zchunk_candidates(N))
+        return 1.0 + (0 if schedule == 0 else 0.5) + (nvar - 1 - v) * 0.1 + \
+            (0 if zc == zcs[1] else 0.05)
+
+    monkeypatch.setattr(autotune, "measure", fake)
+    e = autotune.tune(96, 0, _lib.FP32)
+    assert (e["variant"], e["zchunk"], e["schedule"]) == \
+        (nvar - 1, list(autotune.zchunk_candidates(96))[1], 0)
+    assert len(e["sweep"]) == 2 * nvar * len(list(autotune.zchunk_candidates(96)))
+    cache = json.load(open(tmp_path / "c.json"))
+    assert list(cache) == ["test-gpu|N=96|bc=0|prec=fp32"]
+    assert autotune.best(96, 0, _lib.FP32) == (e["variant"], e["zchunk"], 0)
+    assert autotune.best(97, 0, _lib.FP32) == (0, 0, 1)  # nothing cached: library defaults
+
+
+def test_zchunk_candidates_cover_whole_and_split_columns():
+    c = list(autotune_mod().zchunk_candidates(512))
+    assert c[0] == 0 and 512 in c and all(z >= 16 or z == 0 for z in c)
+    assert c == sorted(set(c))
+
+
+def autotune_mod():
+    from paper_1803_01291_gb300 import autotune
+    return autotune
+
+
+# ---------------------------------------------------------------- server admission
+class FakeSolver:
+    created = 0
+    fail_at = None
+    live = 0
+
+    def __init__(self, N, L, mu, lam, bc, prec):
+        FakeSolver.created += 1
+        if FakeSolver.created == FakeSolver.fail_at:
+            raise _lib.HBEError(_lib.ENOMEM, "injected")
+        self.N, self.steps, self.target = N, 0, 0
+        self.handle = ctypes.c_void_p(1000 + FakeSolver.created)
+        FakeSolver.live += 1
+
+    def set_tuning(self, v, zc):
+        self.variant = v
+
+    def set_initial_bumps(self, bumps):
+        pass
+
+    def sync(self):
+        return _lib.OK
+
+    def progress(self):
+        return self.steps, 0.0
+
+    def diag(self):
+        return {"max_abs_phi": float(self.N)}
+
+    def close(self):
+        FakeSolver.live -= 1
+
+
+class FakeBatch:
+    def __init__(self, prec, K):
+        self.K, self.members, self.launches = K, [], 0
+        self.max_seen = 0
+
+    def add(self, s, nsteps, dt):
+        s.target = nsteps
+        self.members.append(s)
+        self.max_seen = max(self.max_seen, len(self.members))
+
+    def run(self):
+        done = []
+        for s in self.members:
+            s.steps = min(s.target, s.steps + self.K)
+        self.launches += 2 * self.K
+        done = [s for s in self.members if s.steps >= s.target]
+        self.members = [s for s in self.members if s.steps < s.target]
+        return done
+
+    def __len__(self):
+        return len(self.members)
+
+    def close(self):
+        pass
+
+
+@pytest.fixture
+def server_mod(monkeypatch):
+    from paper_1803_01291_gb300 import serve
+    FakeSolver.created, FakeSolver.fail_at, FakeSolver.live = 0, None, 0
+    monkeypatch.setattr(serve, "Solver", FakeSolver)
+    monkeypatch.setattr(serve, "Batch", FakeBatch)
+    return serve
+
+
+def _requests(serve, sizes, nsteps=20):
+    return [serve.SolveRequest(i, 0.001 * i, N, 20.0, 1.0, 1.0, T=nsteps * 0.01, dt=0.01,
+                               bumps=[(1.0, 2.0, (0.0, 0.0, 0.0))])
+            for i, N in enumerate(sizes)]
+
+
+def test_admission_respects_the_memory_budget(server_mod):
+    serve = server_mod
+    reqs = _requests(serve, [64, 48, 64, 32, 64, 48])
+    need = serve.workspace_bytes(64, 0, _lib.FP32)
+    srv = serve.Server(_lib.FP32, K=4, hbm_budget=2 * need)
+    stats = srv.run(reqs, realtime=False)
+    assert sorted(r.rid for r in stats.results) == list(range(len(reqs)))
+    assert stats.peak_bytes <= 2 * need
+    assert all(r.steps == 20 for r in stats.results)
+    assert FakeSolver.live == 0  # every member released
+    # closed loop: every request counts as arrived at time 0
+    assert all(r.arrival == 0.0 for r in stats.results)
+
+
+def test_requeue_after_allocation_failure(server_mod):
+    serve = server_mod
+    FakeSolver.fail_at = 3
+    reqs = _requests(serve, [32, 32, 32, 32])
+    srv = serve.Server(_lib.FP32, K=4, hbm_budget=1 << 40)
+    stats = srv.run(reqs, realtime=False)
+    assert stats.admission_retries == 1
+    assert sorted(r.rid for r in stats.results) == [0, 1, 2, 3]
+
+
+def test_allocation_failure_with_nothing_to_wait_for_raises(server_mod):
+    serve = server_mod
+    FakeSolver.fail_at = 1
+    srv = serve.Server(_lib.FP32, K=4, hbm_budget=1 << 40)
+    with pytest.raises(_lib.HBEError):
+        srv.run(_requests(serve, [32]), realtime=False)
+
+
+def test_request_larger_than_the_budget_is_refused(server_mod):
+    serve = server_mod
+    srv = serve.Server(_lib.FP32, K=4, hbm_budget=1000)
+    with pytest.raises(ValueError):
+        srv.run(_requests(serve, [64]), realtime=False)
+
+
+def test_small_grids_get_the_smallest_tile(server_mod):
+    serve = server_mod
+    srv = serve.Server(_lib.FP32, K=4, hbm_budget=1 << 40)
+    vs = serve.variants(_lib.FP32)
+    small = srv._default_variant(64)
+    assert vs[small]["tile_x"] * vs[small]["tile_y"] == min(v["tile_x"] * v["tile_y"] for v in vs)
+    assert srv._default_variant(256) == 0
+
+
+# ---------------------------------------------------------------- request stream
+def test_request_stream_is_seeded_and_in_range():
+    a = hi.request_stream(50, seed=3)
+    b = hi.request_stream(50, seed=3)
+    assert [(r.N, r.mu, r.lam, r.T) for r in a] == [(r.N, r.mu, r.lam, r.T) for r in b]
+    assert all(r.N in hi.SERVE_SIZES for r in a)
+    assert all(0.5 <= r.mu <= 2 and 0.5 <= r.lam <= 2 and 1 <= r.T <= 6 for r in a)
+    assert all(1 <= len(r.bumps) <= 4 for r in a)
+    assert np.all(np.diff([r.arrival for r in a]) > 0)
+    for r in a[:5]:
+        n, dt = r.steps()
+        h = hi.grid_spacing(r.N, r.L, 0)
+        assert dt <= h / 4 + 1e-15 and abs(n * dt - r.T) < 1e-9
