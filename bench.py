@@ -204,9 +204,11 @@ def workload(N: int):
 
 
 def time_path(hbe, torch, prob, prec_id, steps, warmup, schedule=1, tuning=None):
-    """Warm up, then time `steps` RK4 steps with the step's kernels each
-    bracketed by CUDA events on the solver's stream.  Returns (seconds,
-    per-launch ms, launches in the timed region)."""
+    """Warm up, then time `steps` RK4 steps through the production path (the
+    context's CUDA graph of K steps, hbe_step_async) with CUDA events on the
+    solver's stream.  The per-kernel times for the roofline come from a
+    separate run with every kernel bracketed by events (hbe_profile_stages).
+    Returns (seconds, per-launch ms, launches in the timed region)."""
     s = hbe.Solver(prob.N, prob.L, prob.mu, prob.lam, prob.bc, prec_id)
     s.set_schedule(schedule)
     if tuning is not None:
@@ -216,19 +218,22 @@ def time_path(hbe, torch, prob, prec_id, steps, warmup, schedule=1, tuning=None)
     s.set_initial(phi0, phi1)
     del phi0, phi1
     if warmup:
-        s.profile_stages(warmup, prob.dt)
+        s.step(warmup, prob.dt)  # also captures the graph
+    stage_ms = s.profile_stages(min(steps, 50), prob.dt)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     l0 = s.launches
     e0.record(stream)
-    stage_ms = s.profile_stages(steps, prob.dt)
+    s.step_async(steps, prob.dt)
     e1.record(stream)
+    s.sync()
     torch.cuda.synchronize()
     secs = e0.elapsed_time(e1) / 1e3
-    # the step's kernels (counted by the library) + the per-step bookkeeping
-    # kernel + one run-setup kernel
-    launches = s.launches - l0 + steps + 1
+    # the library's count (stage and ghost-copy kernels of every graph replay,
+    # K steps each) + one bookkeeping kernel per replay + one run-setup kernel
+    K = 8
+    launches = s.launches - l0 + (steps + K - 1) // K + 1
     s.close()
     return secs, stage_ms, launches
 
