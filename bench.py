@@ -69,6 +69,9 @@ def measured_peaks():
 # FP64 FMA rate of GB300 measured with a dependent-free FMA loop (0.58 TFMA/s,
 # 152 SMs, ~1.9 GHz): the FP64 stage kernels are bound by it, not by HBM.
 FP64_FMA_PER_S = 0.58e12
+# FP64 instructions (DADD + DFMA + DMUL) per point-step of the fused FP64
+# kernels, counted by ncu on the 256^3 periodic workload (38.3 + 61.0)
+FP64_INSTR_PER_POINT_STEP = 99.3
 
 
 def kernel_source_hash(prec: str = "fp32") -> str:
@@ -545,9 +548,13 @@ def main():
                      "ms_per_step": s2 / steps * 1e3, "stage_ms": ms2,
                      "hbm_frac": sum(sbp) * float(N) ** 3 * steps / s2 / 1e9 / hbm_peak}
             if name == "fp64":
-                # ALU roofline: FP64 FMA-pipe instructions per point-step of the kernels
-                entry["alu_bound_note"] = ("FP64 runs at 0.58 TFMA/s on GB300 (measured); "
-                                           "see DESIGN.md for the per-point op count")
+                # FP64-pipe roofline: FP64 instructions per point-step of the two fused
+                # kernels (ncu count) against the measured FP64 instruction rate
+                ach = FP64_INSTR_PER_POINT_STEP * v * 1e9
+                entry["roofline"] = {"bound": "alu", "pipe": "fp64", "achieved": ach / 1e12,
+                                     "peak": FP64_FMA_PER_S / 1e12, "unit": "T FP64 instr/s",
+                                     "frac": ach / FP64_FMA_PER_S,
+                                     "per_point_step": FP64_INSTR_PER_POINT_STEP}
             extra[name] = entry
         line["precisions"] = extra
 
