@@ -537,7 +537,7 @@ def main():
 
     if not args.no_extra:
         extra = {}
-        for name, pid, steps in (("fp64", hbe.FP64, max(10, args.steps // 10)),
+        for name, pid, steps in (("fp64", hbe.FP64, max(10, min(100, args.steps))),
                                  ("bf16", hbe.BF16, args.steps),
                                  ("fp32_plain", hbe.FP32_PLAIN, args.steps)):
             s2, ms2, _ = time_path(hbe, torch, prob, pid, steps, 3, args.schedule,
