@@ -122,6 +122,8 @@ struct StageCfg {
   static_assert(SMEM <= 227 * 1024, "ring of 4 slots does not fit in 227 KB of shared memory");
   static constexpr int MINB = MINB_;  // blocks per SM the registers must allow
   static constexpr bool ROTATE = PR::ROTATE;
+  // packed FP32 arithmetic for pairs of x points (FP32 math, even VEC, difference form)
+  static constexpr bool PACKED = sizeof(TM) == 4 && VEC % 2 == 0 && DIFF;
   static_assert(VEC == 1 || VEC == 2 || VEC == 4, "1, 2 or 4 x points per lane");
   static_assert(VEC * (int)sizeof(TM) <= 16, "lane vector of <= 16 bytes");
   static_assert(HXS >= 2 && HXG >= 2 && HXS % VEC == 0 && HXG % VEC == 0, "halo alignment");
@@ -423,6 +425,33 @@ __device__ __forceinline__ TM lap_g(TM c43, TM cm12, TM ccen, TM nlam, TM m3, bo
   return fmaT(c43, s1, g);
 }
 
+// The same evaluation for two neighbouring x points at once with the packed
+// FP32 instructions of sm_100 and later (two lanes of arithmetic per
+// instruction, each rounded exactly as the scalar operation: a - b is formed
+// as fma(b, -1, a), one rounding of the exact difference).  Difference form
+// only (the FP32 paths).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 lap_g2(float2 c43, float2 cm12, float2 ccen, float2 nlam,
+                                         float2 m3, float2 P0, float2 xm2, float2 xm1,
+                                         float2 xp1, float2 xp2, float2 ym2, float2 ym1,
+                                         float2 yp1, float2 yp2, float2 zm2, float2 zm1,
+                                         float2 zp1, float2 zp2, float2 Q) {
+  const float2 s1 = __fadd2_rn(__fadd2_rn(sub2(xm1, P0), sub2(xp1, P0)),
+                               __fadd2_rn(__fadd2_rn(sub2(ym1, P0), sub2(yp1, P0)),
+                                          __fadd2_rn(sub2(zm1, P0), sub2(zp1, P0))));
+  const float2 s2 = __fadd2_rn(__fadd2_rn(sub2(xm2, P0), sub2(xp2, P0)),
+                               __fadd2_rn(__fadd2_rn(sub2(ym2, P0), sub2(yp2, P0)),
+                                          __fadd2_rn(sub2(zm2, P0), sub2(zp2, P0))));
+  float2 g = __ffma2_rn(__fmul2_rn(nlam, __fmul2_rn(P0, P0)), P0, __fmul2_rn(m3, Q));
+  g = __ffma2_rn(ccen, P0, g);
+  g = __ffma2_rn(cm12, s2, g);
+  return __ffma2_rn(c43, s1, g);
+}
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
 // One consumer warp.  Kinds (KN = 1 for one stage, 2 for a fused pair) share
 // the ring tiles; the register window holds P of every kind at planes
 // z-2..z+2 for the warp's own points (rotating or shifted, see plane()).
@@ -635,18 +664,47 @@ struct Consumer {
         load_as<TS, TM, VEC>(is + C::IS_BYTES / (int)sizeof(TS), lq);
       }
       TM res[KN][VEC];
+      if constexpr (C::PACKED) {
+        // two x points per packed instruction (bitwise the scalar results)
 #pragma unroll
-      for (int kk = 0; kk < KN; ++kk) {
+        for (int kk = 0; kk < KN; ++kk) {
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-          TM Q;
-          if (kk == 0) Q = (S == 1 || S == 5) ? qS[j] : fmaT(k.q0, X[j], qS[j]);
-          else Q = fmaT(k.q1, res[0][j], qS[j]);
-          res[kk][j] = lap_g(k.c43[kk], k.cm12[kk], k.ccen[kk], k.nlam, k.m3, C::DIFF, c[kk][j],
-                             e[kk][j], e[kk][j + 1], e[kk][j + 3], e[kk][j + 4], Pz(kk, r - 2, j),
-                             Pz(kk, r - 1, j), Pz(kk, r + 1, j), Pz(kk, r + 2, j),
-                             win[WM4][kk][r][j], win[WM3][kk][r][j], win[WM1][kk][r][j],
-                             win[W0][kk][r][j], Q);
+          for (int j = 0; j < VEC; j += 2) {
+            float2 Q;
+            if (kk == 0)
+              Q = (S == 1 || S == 5) ? f2(qS[j], qS[j + 1])
+                                     : __ffma2_rn(f2(k.q0), f2(X[j], X[j + 1]), f2(qS[j], qS[j + 1]));
+            else
+              Q = __ffma2_rn(f2(k.q1), f2(res[0][j], res[0][j + 1]), f2(qS[j], qS[j + 1]));
+            const float2 g = lap_g2(
+                f2(k.c43[kk]), f2(k.cm12[kk]), f2(k.ccen[kk]), f2(k.nlam), f2(k.m3),
+                f2(c[kk][j], c[kk][j + 1]), f2(e[kk][j], e[kk][j + 1]),
+                f2(e[kk][j + 1], e[kk][j + 2]), f2(e[kk][j + 3], e[kk][j + 4]),
+                f2(e[kk][j + 4], e[kk][j + 5]), f2(Pz(kk, r - 2, j), Pz(kk, r - 2, j + 1)),
+                f2(Pz(kk, r - 1, j), Pz(kk, r - 1, j + 1)), f2(Pz(kk, r + 1, j), Pz(kk, r + 1, j + 1)),
+                f2(Pz(kk, r + 2, j), Pz(kk, r + 2, j + 1)),
+                f2(win[WM4][kk][r][j], win[WM4][kk][r][j + 1]),
+                f2(win[WM3][kk][r][j], win[WM3][kk][r][j + 1]),
+                f2(win[WM1][kk][r][j], win[WM1][kk][r][j + 1]),
+                f2(win[W0][kk][r][j], win[W0][kk][r][j + 1]), Q);
+            res[kk][j] = g.x;
+            res[kk][j + 1] = g.y;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < KN; ++kk) {
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) {
+            TM Q;
+            if (kk == 0) Q = (S == 1 || S == 5) ? qS[j] : fmaT(k.q0, X[j], qS[j]);
+            else Q = fmaT(k.q1, res[0][j], qS[j]);
+            res[kk][j] = lap_g(k.c43[kk], k.cm12[kk], k.ccen[kk], k.nlam, k.m3, C::DIFF, c[kk][j],
+                               e[kk][j], e[kk][j + 1], e[kk][j + 3], e[kk][j + 4], Pz(kk, r - 2, j),
+                               Pz(kk, r - 1, j), Pz(kk, r + 1, j), Pz(kk, r + 2, j),
+                               win[WM4][kk][r][j], win[WM3][kk][r][j], win[WM1][kk][r][j],
+                               win[W0][kk][r][j], Q);
+          }
         }
       }
       const bool rok = it.xok && y < it.N;
