@@ -51,8 +51,8 @@ struct PrecFP64 {
   static constexpr bool KAHAN = false;
   static constexpr bool DIFF = false;   // merged-centre stencil (fewest FP64 ops)
   // plane loop unrolled 5 times over a rotating register window (no register
-  // moves) where that measured faster than shifting the window: FP32 with
-  // compensated state only (FP64 spills with it, BF16 / plain FP32 gain nothing)
+  // moves) where that measured faster than shifting the window: the FP32 paths
+  // with compensated state or plain (FP64 spills with it, BF16 measured slower)
   static constexpr bool ROTATE = false;
 };
 struct PrecFP32 {
@@ -71,7 +71,7 @@ struct PrecFP32Plain {
   using TS = float; using TG = float; using TM = float;
   static constexpr bool KAHAN = false;
   static constexpr bool DIFF = true;
-  static constexpr bool ROTATE = false;
+  static constexpr bool ROTATE = true;
 };
 
 __host__ __device__ constexpr int align128(int b) { return (b + 127) & ~127; }
