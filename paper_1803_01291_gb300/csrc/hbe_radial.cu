@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "hbe.h"
 
@@ -82,6 +83,29 @@ __device__ __forceinline__ T lap_dr2(T m2, T m1, T c0, T p1, T p2, bool origin, 
   const T d2 = fm(T(-1.0 / 12.0), (m2 - c0) + (p2 - c0), T(4.0 / 3.0) * ((m1 - c0) + (p1 - c0)));
   const T d1 = fm(T(2.0 / 3.0), p1 - m1, T(-1.0 / 12.0) * (p2 - m2));
   return fm(two_over_i, d1, d2);
+}
+
+// The FP32 evaluation of two neighbouring nodes (j, j+1 of a thread) at once
+// with Blackwell's packed FP32 instructions; every element is rounded as the
+// scalar operation above (a - b as fma(b, -1, a)), so the results are the same
+// bits.  Interior nodes only: the caller replaces the origin's value.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 p2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
+template <int V>
+__device__ __forceinline__ float2 g_pair(const float (&E)[V + 4], int j, float2 w, float2 Q,
+                                         float c, float2 P, float mu2, float lam) {
+  const float2 m2 = p2(E[j], E[j + 1]), m1 = p2(E[j + 1], E[j + 2]), c0 = p2(E[j + 2], E[j + 3]),
+               p1 = p2(E[j + 3], E[j + 4]), q2 = p2(E[j + 4], E[j + 5]);
+  const float2 d2 = __ffma2_rn(p2(-1.0f / 12.0f), __fadd2_rn(sub2(m2, c0), sub2(q2, c0)),
+                               __fmul2_rn(p2(4.0f / 3.0f), __fadd2_rn(sub2(m1, c0), sub2(p1, c0))));
+  const float2 d1 = __ffma2_rn(p2(2.0f / 3.0f), sub2(p1, m1), __fmul2_rn(p2(-1.0f / 12.0f), sub2(q2, m2)));
+  const float2 lap = __ffma2_rn(w, d1, d2);
+  const float2 PP = __fmul2_rn(P, P);
+  const float2 t = __fmul2_rn(P, __ffma2_rn(p2(-lam), PP, p2(mu2)));
+  return __ffma2_rn(p2(c), lap, __ffma2_rn(p2(-3.0f), Q, t));
 }
 
 // Thread t owns the V consecutive nodes V t .. V t + V - 1 (those below n) and
@@ -184,33 +208,54 @@ __global__ void __launch_bounds__(TH, MINB) radial_kernel(Args a) {
     if (k >= a.nsteps) break;
     const T c1 = T(sh.coef[kc][0]), c2 = T(sh.coef[kc][1]), c3 = T(sh.coef[kc][2]),
             c4 = T(sh.coef[kc][3]);
-    // stage 1: argument p -> G1
+    // G of every owned node from the stage argument (in E and A) and the point
+    // argument Q; nodes at or beyond n keep 0
+    auto eval = [&](T (&out)[V], const T (&A)[V], const T (&Qv)[V], T c) {
+      if constexpr (std::is_same<T, float>::value && V % 2 == 0) {
 #pragma unroll
-    for (int j = 0; j < V; ++j)
-      if (i0 + j < n) g1[j] = rhs_g(q[j], c1, lap(E, j), p[j], mu2, lam);
+        for (int j = 0; j < V; j += 2) {
+          const float2 g = g_pair<V>(E, j, p2(w[j], w[j + 1]), p2(Qv[j], Qv[j + 1]), c,
+                                     p2(A[j], A[j + 1]), mu2, lam);
+          out[j] = i0 + j < n ? g.x : T(0);
+          out[j + 1] = i0 + j + 1 < n ? g.y : T(0);
+        }
+        if (tid == 0) out[0] = rhs_g(Qv[0], c, lap(E, 0), A[0], mu2, lam);  // the origin
+      } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+          if (i0 + j < n) out[j] = rhs_g(Qv[j], c, lap(E, j), A[j], mu2, lam);
+      }
+    };
+    T Qs[V];
+    // stage 1: argument p -> G1
+    eval(g1, p, q, c1);
     // stage 2: argument P2 = p + dt/2 q, Q2 = q + dt/2 G1 -> G2
 #pragma unroll
     for (int j = 0; j < V; ++j) P[j] = fm(hdt, q[j], p[j]);
     exchange(P, E, 0);
 #pragma unroll
-    for (int j = 0; j < V; ++j)
-      if (i0 + j < n) g2[j] = rhs_g(fm(hdt, g1[j], q[j]), c2, lap(E, j), P[j], mu2, lam);
+    for (int j = 0; j < V; ++j) Qs[j] = fm(hdt, g1[j], q[j]);
+    eval(g2, P, Qs, c2);
     // stage 3: argument P3 = p + dt/2 q + dt^2/4 G1, Q3 = q + dt/2 G2 -> G3
 #pragma unroll
     for (int j = 0; j < V; ++j) P[j] = fm(qdt2, g1[j], fm(hdt, q[j], p[j]));
     exchange(P, E, 0);
 #pragma unroll
-    for (int j = 0; j < V; ++j)
-      if (i0 + j < n) g3[j] = rhs_g(fm(hdt, g2[j], q[j]), c3, lap(E, j), P[j], mu2, lam);
+    for (int j = 0; j < V; ++j) Qs[j] = fm(hdt, g2[j], q[j]);
+    eval(g3, P, Qs, c3);
     // stage 4: argument P4 = p + dt q + dt^2/2 G2, Q4 = q + dt G3 -> G4; RK4 combine
 #pragma unroll
     for (int j = 0; j < V; ++j) P[j] = fm(hdt2, g2[j], fm(dt, q[j], p[j]));
     exchange(P, E, 0);
     T lmax = T(0);
+    T g4v[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) Qs[j] = fm(dt, g3[j], q[j]);
+    eval(g4v, P, Qs, c4);
 #pragma unroll
     for (int j = 0; j < V; ++j) {
       if (i0 + j < n) {
-        const T g4 = rhs_g(fm(dt, g3[j], q[j]), c4, lap(E, j), P[j], mu2, lam);
+        const T g4 = g4v[j];
         const T s3 = g1[j] + g2[j] + g3[j];
         p[j] = fm(sdt2, s3, fm(dt, q[j], p[j]));
         q[j] = fm(sdt, fm(T(2), g2[j] + g3[j], g1[j] + g4), q[j]);
