@@ -187,48 +187,71 @@ template <> struct Pair<unsigned long long> { using type = ulonglong2; };
 template <> struct Pair<unsigned> { using type = uint2; };
 template <> struct Pair<unsigned short> { using type = unsigned; };
 
+// One pass over the work units u < 4 N^2 of a plane stack: unit u copies one
+// element of the ghost rows (plane z, ghost row g, column x) and, for
+// u < N^2, the four ghost columns of one interior row.  The values of both
+// fields are loaded before anything is stored, so a thread has all its loads
+// in flight at once (the accesses are scattered: one sector per row end).
+// Reads and writes never overlap: ghost rows are written only at x in [0, N)
+// from interior rows, ghost columns only in interior rows from interior columns.
 template <class E>
-__device__ void wrap_field(E *f, int N, int pitch, int64_t plane, int hx, long long tid,
-                           long long nth) {
-  const long long nx = (long long)N * N;
-  if ((N & 1) == 0) {
-    // columns 0,1 / N-2,N-1 / -2,-1 / N,N+1 are aligned pairs when N is even
-    using P = typename Pair<E>::type;
-    for (long long u = tid; u < nx; u += nth) {
-      const int z = (int)(u / N), y = (int)(u % N);
-      E *row = f + (int64_t)z * plane + (int64_t)(y + 2) * pitch + hx;
-      const P lo = *reinterpret_cast<const P *>(row), hi = *reinterpret_cast<const P *>(row + N - 2);
-      *reinterpret_cast<P *>(row - 2) = hi;
-      *reinterpret_cast<P *>(row + N) = lo;
-    }
-  } else {
-    for (long long u = tid; u < nx; u += nth) {
-      const int z = (int)(u / N), y = (int)(u % N);
-      E *row = f + (int64_t)z * plane + (int64_t)(y + 2) * pitch + hx;
-      const E a = row[0], b = row[1], c = row[N - 2], d = row[N - 1];
-      row[-2] = c;
-      row[-1] = d;
-      row[N] = a;
-      row[N + 1] = b;
-    }
-  }
-  // padded rows 0, 1 <- N, N+1 (y = N-2, N-1) and N+2, N+3 <- 2, 3 (y = 0, 1)
-  const long long ny = (long long)N * 4 * N;
-  for (long long u = tid; u < ny; u += nth) {
+__device__ void wrap_pair(void *va, void *vb, int N, int pitch, int64_t plane, int hx,
+                          long long tid, long long nth) {
+  E *fa = static_cast<E *>(va), *fb = static_cast<E *>(vb);
+  const bool two = fb != nullptr;
+  using P = typename Pair<E>::type;
+  const long long nc = (long long)N * N, nr = 4 * nc;
+  for (long long u = tid; u < nr; u += nth) {
+    // ghost rows: padded rows 0, 1 <- N, N+1 (y = N-2, N-1) and N+2, N+3 <- 2, 3 (y = 0, 1)
     const int x = (int)(u % N);
     const long long r = u / N;
     const int z = (int)(r >> 2), g = (int)(r & 3);
     const int dst = g < 2 ? g : N + g, src = g < 2 ? N + g : g;
-    E *col = f + (int64_t)z * plane + hx + x;
-    col[(int64_t)dst * pitch] = col[(int64_t)src * pitch];
+    const int64_t cb = (int64_t)z * plane + hx + x;
+    const E ra = fa[cb + (int64_t)src * pitch];
+    const E rb = two ? fb[cb + (int64_t)src * pitch] : E(0);
+    if (u >= nc) {
+      fa[cb + (int64_t)dst * pitch] = ra;
+      if (two) fb[cb + (int64_t)dst * pitch] = rb;
+      continue;
+    }
+    // ghost columns of row (zc, y): -2, -1 <- N-2, N-1 and N, N+1 <- 0, 1
+    const int zc = (int)(u / N), y = (int)(u % N);
+    const int64_t ro = (int64_t)zc * plane + (int64_t)(y + 2) * pitch + hx;
+    if ((N & 1) == 0) {
+      // the column pairs are aligned when N is even
+      const P alo = *reinterpret_cast<const P *>(fa + ro);
+      const P ahi = *reinterpret_cast<const P *>(fa + ro + N - 2);
+      P blo = alo, bhi = ahi;
+      if (two) {
+        blo = *reinterpret_cast<const P *>(fb + ro);
+        bhi = *reinterpret_cast<const P *>(fb + ro + N - 2);
+      }
+      fa[cb + (int64_t)dst * pitch] = ra;
+      *reinterpret_cast<P *>(fa + ro - 2) = ahi;
+      *reinterpret_cast<P *>(fa + ro + N) = alo;
+      if (two) {
+        fb[cb + (int64_t)dst * pitch] = rb;
+        *reinterpret_cast<P *>(fb + ro - 2) = bhi;
+        *reinterpret_cast<P *>(fb + ro + N) = blo;
+      }
+    } else {
+      E a[4], b[4] = {};
+      const int cs[4] = {0, 1, N - 2, N - 1};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = fa[ro + cs[i]];
+      if (two) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] = fb[ro + cs[i]];
+      }
+      fa[cb + (int64_t)dst * pitch] = ra;
+      fa[ro - 2] = a[2]; fa[ro - 1] = a[3]; fa[ro + N] = a[0]; fa[ro + N + 1] = a[1];
+      if (two) {
+        fb[cb + (int64_t)dst * pitch] = rb;
+        fb[ro - 2] = b[2]; fb[ro - 1] = b[3]; fb[ro + N] = b[0]; fb[ro + N + 1] = b[1];
+      }
+    }
   }
-}
-
-template <class E>
-__device__ void wrap_pair(void *a, void *b, int N, int pitch, int64_t plane, int hx, long long tid,
-                          long long nth) {
-  wrap_field<E>(static_cast<E *>(a), N, pitch, plane, hx, tid, nth);
-  if (b) wrap_field<E>(static_cast<E *>(b), N, pitch, plane, hx, tid, nth);
 }
 
 __global__ void wrap_kernel(Desc *descs, const int *ndesc, int k, int stage) {

@@ -778,12 +778,18 @@ struct Consumer {
     const int nitems = *prm.nitems;
     int slot = 0;
     uint32_t phase = 0;
+    const Desc *coef_d = nullptr;
+    long long coef_n = -1;
     for (int itx = blockIdx.x; itx < nitems; itx += gridDim.x) {
       const WorkItem w = prm.items[itx];
       Desc *d = prm.descs + w.x;
       if (!item_active<S>(d, prm.k, warp == 0 && lane_ == 0)) continue;
       const long long n = d->n_base + prm.k;
-      {
+      if (d != coef_d || n != coef_n) {
+        // the coefficients of (context, step): formed once per warp and launch
+        // when every work item belongs to one context
+        coef_d = d;
+        coef_n = n;
         UCoef<TM> c0;
         if (lane_ == 0) c0 = unified_coef<C>(d, n);
         const TM *src = reinterpret_cast<const TM *>(&c0);
