@@ -66,6 +66,7 @@ struct hbe_ctx {
   void *f[NUM_FIELDS] = {};
   CUtensorMap *d_tmaps = nullptr;
   unsigned long long *d_maxabs = nullptr;
+  double *d_coef = nullptr;          // step coefficients (Desc::coef)
   Desc *d_desc = nullptr;
   Desc *h_desc = nullptr;  // pinned mirror
   WorkItem *d_items = nullptr;
@@ -321,6 +322,8 @@ hbe_status ensure_graph(hbe_ctx *ctx) {
   CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
   hbe_status st = HBE_OK;
   const int first = ctx->schedule ? 4 : 0, last = ctx->schedule ? 6 : 4;
+  cudaError_t ec = launch_coef(ctx->d_desc, ctx->d_one, 1, ctx->K, ctx->cap_stream);
+  if (ec != cudaSuccess) st = set_err(ctx->err, HBE_ECUDA, "%s", cudaGetErrorString(ec));
   for (int k = 0; k < ctx->K && st == HBE_OK; ++k)
     for (int s = first; s < last && st == HBE_OK; ++s) {
       StageParams p{ctx->d_desc, ctx->d_items, ctx->d_nitems, ctx->d_err, k};
@@ -495,6 +498,8 @@ hbe_status create_common(int N, double L, double mu, double lambda, int bc, int 
   CKB(cudaMalloc(&ctx->d_tmaps, NUM_TMAPS * sizeof(CUtensorMap)));
   CKB(cudaMalloc(&ctx->d_maxabs, kMaxK * sizeof(unsigned long long)));
   CKB(cudaMemset(ctx->d_maxabs, 0, kMaxK * sizeof(unsigned long long)));
+  CKB(cudaMalloc(&ctx->d_coef, kCoefDoubles * sizeof(double)));
+  CKB(cudaMemset(ctx->d_coef, 0, kCoefDoubles * sizeof(double)));
   CKB(cudaMalloc(&ctx->d_desc, sizeof(Desc)));
   CKB(cudaMallocHost(&ctx->h_desc, sizeof(Desc)));
   CKB(cudaMalloc(&ctx->d_nitems, sizeof(int)));
@@ -514,6 +519,7 @@ hbe_status create_common(int N, double L, double mu, double lambda, int bc, int 
   d.t0 = 0.0; d.dt = 0.0;
   d.n_base = 0; d.n_end = 0; d.stop_k = kNoStop; d.stop_thr = 0.0;
   d.maxabs = ctx->d_maxabs;
+  d.coef = ctx->d_coef;
   d.tmaps = ctx->d_tmaps;
   for (int i = 0; i < NUM_FIELDS; ++i) d.f[i] = ctx->f[i];
   if ((st = push_desc(ctx)) != HBE_OK) return bail(st);
@@ -560,6 +566,7 @@ void hbe_destroy(hbe_ctx *ctx) {
   if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
   cudaFree(ctx->d_tmaps);
   cudaFree(ctx->d_maxabs);
+  cudaFree(ctx->d_coef);
   cudaFree(ctx->d_desc);
   if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
   cudaFree(ctx->d_items);
@@ -855,6 +862,7 @@ hbe_status hbe_profile_stages(hbe_ctx *ctx, int64_t nsteps, double dt, float *ms
   const VariantTable &vt = table_for(ctx->prec);
   int64_t wraps = 0;
   for (int64_t n = 0; n < nsteps && st == HBE_OK; ++n) {
+    CK(launch_coef(ctx->d_desc, ctx->d_one, 1, 1, ctx->stream));
     for (int s = 0; s < nl && st == HBE_OK; ++s) {
       CK(cudaEventRecord(ev[(n * nl + s) * 2], ctx->stream));
       StageParams p{ctx->d_desc, ctx->d_items, ctx->d_nitems, ctx->d_err, 0};
@@ -1258,6 +1266,8 @@ static hbe_status batch_rebuild(hbe_batch *b) {
     cudaGraph_t g = nullptr;
     CKX(b->err, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     hbe_status st = HBE_OK;
+    cudaError_t ec = launch_coef(b->d_descs, b->d_ndesc, b->cap_desc, b->K, b->cap_stream);
+    if (ec != cudaSuccess) st = set_err(b->err, HBE_ECUDA, "%s", cudaGetErrorString(ec));
     // the batch always runs the fused stage pairs (kernels 4 and 5 of a variant)
     for (int k = 0; k < b->K && st == HBE_OK; ++k)
       for (int s = 4; s < 6 && st == HBE_OK; ++s) {

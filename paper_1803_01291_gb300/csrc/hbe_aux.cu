@@ -168,6 +168,45 @@ __global__ void advance_kernel(Desc *descs, const int *ndesc, int K) {
   for (int k = 0; k < K; ++k) d.maxabs[k] = 0ull;
 }
 
+// The step coefficients of steps k = 0 .. K-1 of the coming batch (t from the
+// context's t0, dt and n_base, all in FP64), and the dt-only constants.  One
+// thread per (context, step); run before the batch's first stage launch.
+__global__ void coef_kernel(Desc *descs, const int *ndesc, int K) {
+  const int i = blockIdx.y, k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *ndesc || k >= K) return;
+  const Desc &d = descs[i];
+  double *c = d.coef;
+  const double dt = d.dt;
+  const double tn = d.t0 + (double)(d.n_base + k) * dt;
+  const double st[4] = {tn, tn + 0.5 * dt, tn + 0.5 * dt, tn + dt};
+  for (int s = 0; s < 4; ++s) {
+    const double e = exp(-2.0 * st[s]) * d.inv_h2;
+    double *o = c + k * kCoefPerStep + s * kCoefPerStage;
+    o[0] = 4.0 / 3.0 * e;
+    o[1] = -e / 12.0;
+    o[2] = d.mu2 - 7.5 * e;
+  }
+  if (k == 0) {
+    double *o = c + kMaxK * kCoefPerStep;
+    const double sq[4] = {0.0, 0.5 * dt, 0.5 * dt, dt};
+    const double sg[4] = {0.0, 0.0, 0.25 * dt * dt, 0.5 * dt * dt};
+    for (int s = 0; s < 4; ++s) {
+      o[kCoefSq + s] = sq[s];
+      o[kCoefSg + s] = sg[s];
+      o[kCoefSp + s] = sq[s];
+    }
+    o[kCoefB6] = dt * dt / 6.0;
+    o[kCoefD6] = dt / 6.0;
+    o[kCoefDt] = dt;
+    o[kCoefNlam] = -d.lambda;
+  }
+}
+
+cudaError_t launch_coef(Desc *descs, const int *ndesc, int max_desc, int K, cudaStream_t st) {
+  coef_kernel<<<dim3((K + 63) / 64, max_desc), 64, 0, st>>>(descs, ndesc, K);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_advance(Desc *descs, const int *ndesc, int max_desc, int K, cudaStream_t st) {
   const int threads = 128;
   advance_kernel<<<(max_desc + threads - 1) / threads, threads, 0, st>>>(descs, ndesc, K);

@@ -11,6 +11,9 @@ cudaError_t launch_unpack(int prec, const void *hi, const void *lo, double *dst,
                           int hx, int z_begin, int z_count, cudaStream_t st);
 cudaError_t launch_bumps(int prec, void *hi, void *lo, int N, int pitch, int hx, int periodic,
                          double h, int nb, const double *d_prm, cudaStream_t st);
+// The step coefficients of steps 0 .. K-1 of the coming batch of each context
+// (Desc::coef); launched before the batch's stage kernels.
+cudaError_t launch_coef(Desc *descs, const int *ndesc, int max_desc, int K, cudaStream_t st);
 cudaError_t launch_advance(Desc *descs, const int *ndesc, int max_desc, int K, cudaStream_t st);
 // Periodic ghost copies of the fields stage `stage` (1..6, 5 and 6 the fused
 // pairs) wrote for step k of the batch; contexts that are not periodic or did

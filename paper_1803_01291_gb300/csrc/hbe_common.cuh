@@ -39,6 +39,25 @@ enum StopStatus : int { ST_RUNNING = 0, ST_STOPPED = 1, ST_NONFINITE = 2 };
 constexpr long long kNoStop = 0x7fffffffffffffffLL;
 constexpr int kMaxK = 64;  // steps per captured graph
 
+// Step coefficients of the stage kernels (Sec. 2.1, S7), tabled in FP64 by
+// coef_kernel for the steps of a batch.  Per step k: for each RK stage s of
+// the step (stage times t, t + dt/2, t + dt/2, t + dt with t = t0 + n dt,
+// n = n_base + k) and c = e^{-2 t_s} / h^2: 4/3 c, -c/12, mu^2 - 15/2 c.
+// After the kMaxK steps: the dt-only constants, in the order of kCoef*.
+constexpr int kCoefPerStage = 3;
+constexpr int kCoefPerStep = 4 * kCoefPerStage;
+enum CoefConst : int {
+  kCoefSq = 0,    // [4] q weight of the stage argument P_s: 0, dt/2, dt/2, dt
+  kCoefSg = 4,    // [4] G weight of P_s: 0, 0, dt^2/4, dt^2/2
+  kCoefSp = 8,    // [4] G weight of the point argument Q_s: 0, dt/2, dt/2, dt
+  kCoefB6 = 12,   // dt^2/6
+  kCoefD6 = 13,   // dt/6
+  kCoefDt = 14,   // dt
+  kCoefNlam = 15, // -lambda
+  kCoefConsts = 16
+};
+constexpr int kCoefDoubles = kMaxK * kCoefPerStep + kCoefConsts;
+
 // Per-context state the kernels read; host keeps a mirror.  All stage kernels
 // of one batch read it; only the per-batch advance kernel writes n_base,
 // n_end, stop_k and status (stage-1 kernels may lower stop_k).
@@ -56,6 +75,7 @@ struct alignas(64) Desc {
   int32_t status;                // StopStatus after the last batch
   int32_t pad1;
   unsigned long long *maxabs;    // [kMaxK] max|phi| after step k of the batch (double bits)
+  double *coef;                  // [kCoefDoubles] step coefficients (coef_kernel)
   const CUtensorMap *tmaps;      // [NUM_TMAPS], 64-byte aligned, in device memory
   void *f[NUM_FIELDS];
 };

@@ -54,7 +54,8 @@ constexpr size_t kOffTmaps = kOffDesc + 256;                     // NUM_TMAPS x 
 constexpr size_t kOffMaxabs = kOffTmaps + NUM_TMAPS * 128;       // kMaxK x 8 bytes
 constexpr size_t kOffErr = kOffMaxabs + kMaxK * 8;               // unsigned
 constexpr size_t kOffCounts = kOffErr + 16;                      // int nitems, int one
-constexpr size_t kOffItems = kOffCounts + 16;                    // work items (int4)
+constexpr size_t kOffCoef = kOffCounts + 16;                     // kCoefDoubles x 8 bytes
+constexpr size_t kOffItems = kOffCoef + kCoefDoubles * 8;        // work items (int4)
 constexpr int kMaxItems = (int)((kMetaBytes - (kOffItems - kOffDesc)) / sizeof(WorkItem));
 static_assert(kOffItems + kMaxItems * sizeof(WorkItem) <= kNoAllocScratchBytes, "layout");
 
@@ -139,6 +140,7 @@ extern "C" hbe_status hbe_step_fp64_noalloc(int N, double L, double mu, double l
   unsigned *d_err = reinterpret_cast<unsigned *>(scr + kOffErr);
   int *d_counts = reinterpret_cast<int *>(scr + kOffCounts);
   WorkItem *d_items = reinterpret_cast<WorkItem *>(scr + kOffItems);
+  double *d_coef = reinterpret_cast<double *>(scr + kOffCoef);
 
   // tensor maps of the fields in the scratch: halo boxes for the fields read
   // with a stencil, interior boxes for the fields read at the point (the
@@ -171,7 +173,7 @@ extern "C" hbe_status hbe_step_fp64_noalloc(int N, double L, double mu, double l
   hd.inv_h2 = 1.0 / (h * h); hd.mu2 = mu * mu; hd.lambda = lambda;
   hd.t0 = t0; hd.dt = dt;
   hd.n_base = 0; hd.n_end = nsteps; hd.stop_k = kNoStop; hd.stop_thr = 0.0;
-  hd.maxabs = d_maxabs; hd.tmaps = d_tm;
+  hd.maxabs = d_maxabs; hd.coef = d_coef; hd.tmaps = d_tm;
   for (int i = 0; i < NUM_FIELDS; ++i) hd.f[i] = f[i];
 
   // the scratch keeps the last call's contents: clear what must start at 0
@@ -196,6 +198,7 @@ extern "C" hbe_status hbe_step_fp64_noalloc(int N, double L, double mu, double l
     grid[s4] = std::max(1, std::min(nb * sms, counts[0]));
   }
   for (int64_t n = 0; n < nsteps; ++n) {
+    NA_CK(launch_coef(d_desc, d_counts + 1, 1, 1, st));
     for (int s4 = 0; s4 < 4; ++s4) {
       StageParams prm{d_desc, d_items, d_counts, d_err, 0};
       void *args[] = {&prm};

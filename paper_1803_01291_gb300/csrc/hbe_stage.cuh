@@ -371,40 +371,42 @@ struct UCoef {
   TM b6, d6, dt;
 };
 
+// Value `lane` of UCoef (in member order) for step `kstep` of the batch, from
+// the FP64 table of coef_kernel (stage times t, t + dt/2, t + dt/2, t + dt of
+// step n_base + kstep), rounded to the math type: each lane reads one entry,
+// and the warp assembles the struct with shuffles.
 template <class C>
-__device__ __forceinline__ UCoef<typename C::TM> unified_coef(const Desc *d, long long n) {
+__device__ __forceinline__ typename C::TM coef_entry(const Desc *d, int kstep, int lane) {
   using TM = typename C::TM;
   constexpr int S = C::S;
-  const double dt = d->dt;
-  const double tn = d->t0 + (double)n * dt;
-  // stage times t, t + dt/2, t + dt/2, t + dt of stages 1..4
-  const double st[4] = {tn, tn + 0.5 * dt, tn + 0.5 * dt, tn + dt};
   const int s0 = S <= 4 ? S - 1 : (S == 5 ? 0 : 2);  // stage of kind 0
-  UCoef<TM> k;
-  for (int i = 0; i < 2; ++i) {
-    const double c = exp(-2.0 * st[(s0 + i) & 3]) * d->inv_h2;
-    k.c43[i] = (TM)(4.0 / 3.0 * c);
-    k.cm12[i] = (TM)(-c / 12.0);
-    k.ccen[i] = C::DIFF ? (TM)d->mu2 : (TM)(d->mu2 - 7.5 * c);
+  const int s1 = (s0 + 1) & 3;                        // stage of kind 1
+  const int st = kstep * kCoefPerStep, cc = kMaxK * kCoefPerStep;
+  // offset into the table; -1: mu^2 (the centre weight of the difference
+  // form), -2: the constant -3
+  int off;
+  switch (lane) {
+    case 0: off = st + s0 * kCoefPerStage; break;            // c43[0] = 4/3 c
+    case 1: off = st + s1 * kCoefPerStage; break;            // c43[1]
+    case 2: off = st + s0 * kCoefPerStage + 1; break;        // cm12[0] = -c/12
+    case 3: off = st + s1 * kCoefPerStage + 1; break;        // cm12[1]
+    case 4: off = C::DIFF ? -1 : st + s0 * kCoefPerStage + 2; break;  // ccen[0]
+    case 5: off = C::DIFF ? -1 : st + s1 * kCoefPerStage + 2; break;  // ccen[1]
+    case 6: off = cc + kCoefSq + s0; break;                  // kq[0]: q weight of P
+    case 7: off = cc + kCoefSq + s1; break;                  // kq[1]
+    case 8: off = cc + kCoefSg + s0; break;                  // kg[0]: G weight of P
+    case 9: off = cc + kCoefSg + s1; break;                  // kg[1]
+    case 10: off = cc + kCoefSp + s0; break;                 // q0: G weight of Q
+    case 11: off = cc + kCoefSp + s1; break;                 // q1
+    case 12: off = cc + kCoefNlam; break;                    // -lambda
+    case 13: off = -2; break;                                // m3 = -3
+    case 14: off = cc + kCoefB6; break;                      // dt^2/6
+    case 15: off = cc + kCoefD6; break;                      // dt/6
+    case 16: off = cc + kCoefDt; break;                      // dt
+    default: off = -2; break;
   }
-  // stage arguments: stage 1 p; stage 2 p + dt/2 q; stage 3 p + dt/2 q + dt^2/4 G1;
-  // stage 4 p + dt q + dt^2/2 G2
-  const double sq[4] = {0.0, 0.5 * dt, 0.5 * dt, dt};
-  const double sg[4] = {0.0, 0.0, 0.25 * dt * dt, 0.5 * dt * dt};
-  // point arguments: stage 2 q + dt/2 G1; stage 3 q + dt/2 G2; stage 4 q + dt G3
-  const double sp[4] = {0.0, 0.5 * dt, 0.5 * dt, dt};
-  for (int i = 0; i < 2; ++i) {
-    k.kq[i] = (TM)sq[(s0 + i) & 3];
-    k.kg[i] = (TM)sg[(s0 + i) & 3];
-  }
-  k.q0 = (TM)sp[s0];
-  k.q1 = (TM)sp[(s0 + 1) & 3];
-  k.nlam = (TM)(-d->lambda);
-  k.m3 = (TM)(-3.0);
-  k.b6 = (TM)(dt * dt / 6.0);
-  k.d6 = (TM)(dt / 6.0);
-  k.dt = (TM)dt;
-  return k;
+  const double v = off >= 0 ? __ldcg(d->coef + off) : (off == -1 ? d->mu2 : -3.0);
+  return (TM)v;
 }
 
 template <class TM>
@@ -786,16 +788,15 @@ struct Consumer {
       if (!item_active<S>(d, prm.k, warp == 0 && lane_ == 0)) continue;
       const long long n = d->n_base + prm.k;
       if (d != coef_d || n != coef_n) {
-        // the coefficients of (context, step): formed once per warp and launch
+        // the coefficients of (context, step): read once per warp and launch
         // when every work item belongs to one context
         coef_d = d;
         coef_n = n;
-        UCoef<TM> c0;
-        if (lane_ == 0) c0 = unified_coef<C>(d, n);
-        const TM *src = reinterpret_cast<const TM *>(&c0);
+        static_assert(sizeof(UCoef<TM>) / sizeof(TM) == 17, "coef_entry covers UCoef");
+        const TM mine = coef_entry<C>(d, prm.k, lane_);
         TM *dst = reinterpret_cast<TM *>(&self.k);
 #pragma unroll
-        for (int i = 0; i < (int)(sizeof(UCoef<TM>) / sizeof(TM)); ++i) dst[i] = shfl_idx(src[i], 0);
+        for (int i = 0; i < 17; ++i) dst[i] = shfl_idx(mine, i);
       }
       Item it;
       it.N = d->N;
