@@ -234,9 +234,10 @@ def time_path(hbe, torch, prob, prec_id, steps, warmup, schedule=1, tuning=None)
     torch.cuda.synchronize()
     secs = e0.elapsed_time(e1) / 1e3
     # the library's count (stage and ghost-copy kernels of every graph replay,
-    # K steps each) + one bookkeeping kernel per replay + one run-setup kernel
+    # K steps each) + two bookkeeping kernels per replay (step coefficients,
+    # advance) + one run-setup kernel
     K = 8
-    launches = s.launches - l0 + (steps + K - 1) // K + 1
+    launches = s.launches - l0 + 2 * ((steps + K - 1) // K) + 1
     s.close()
     return secs, stage_ms, launches
 

@@ -226,68 +226,97 @@ template <> struct Pair<unsigned long long> { using type = ulonglong2; };
 template <> struct Pair<unsigned> { using type = uint2; };
 template <> struct Pair<unsigned short> { using type = unsigned; };
 
-// One pass over the work units u < 4 N^2 of a plane stack: unit u copies one
-// element of the ghost rows (plane z, ghost row g, column x) and, for
-// u < N^2, the four ghost columns of one interior row.  The values of both
-// fields are loaded before anything is stored, so a thread has all its loads
-// in flight at once (the accesses are scattered: one sector per row end).
-// Reads and writes never overlap: ghost rows are written only at x in [0, N)
-// from interior rows, ghost columns only in interior rows from interior columns.
+// Work unit u of a plane stack covers (a) the four ghost columns of interior
+// row u (u < N^2) and (b) piece u of the ghost rows: 16-byte vectors when a
+// row is a whole number of them (rows start 16-byte aligned), else single
+// elements, over x in [0, N) of the 4 ghost rows of every plane.  A thread
+// loads everything its unit needs from both fields before it stores anything,
+// so all its scattered loads are in flight at once.  Reads and writes never
+// overlap: ghost rows are written only at x in [0, N) from interior rows,
+// ghost columns only in interior rows from interior columns.
 template <class E>
 __device__ void wrap_pair(void *va, void *vb, int N, int pitch, int64_t plane, int hx,
                           long long tid, long long nth) {
   E *fa = static_cast<E *>(va), *fb = static_cast<E *>(vb);
   const bool two = fb != nullptr;
   using P = typename Pair<E>::type;
-  const long long nc = (long long)N * N, nr = 4 * nc;
-  for (long long u = tid; u < nr; u += nth) {
-    // ghost rows: padded rows 0, 1 <- N, N+1 (y = N-2, N-1) and N+2, N+3 <- 2, 3 (y = 0, 1)
-    const int x = (int)(u % N);
-    const long long r = u / N;
-    const int z = (int)(r >> 2), g = (int)(r & 3);
-    const int dst = g < 2 ? g : N + g, src = g < 2 ? N + g : g;
-    const int64_t cb = (int64_t)z * plane + hx + x;
-    const E ra = fa[cb + (int64_t)src * pitch];
-    const E rb = two ? fb[cb + (int64_t)src * pitch] : E(0);
-    if (u >= nc) {
-      fa[cb + (int64_t)dst * pitch] = ra;
-      if (two) fb[cb + (int64_t)dst * pitch] = rb;
-      continue;
+  constexpr int VE = 16 / (int)sizeof(E);
+  const bool vec = N % VE == 0;
+  const int nv = vec ? N / VE : N;                       // row pieces per ghost row
+  const long long nc = (long long)N * N, nr = 4LL * N * nv;
+  const long long nu = nc > nr ? nc : nr;
+  const bool even = (N & 1) == 0;                        // column pairs aligned
+  for (long long u = tid; u < nu; u += nth) {
+    // (b) ghost rows: padded rows 0, 1 <- N, N+1 (y = N-2, N-1), N+2, N+3 <- 2, 3 (y = 0, 1)
+    const bool hr = u < nr;
+    int64_t rs = 0, rd = 0;
+    if (hr) {
+      const int piece = (int)(u % nv);
+      const long long r = u / nv;
+      const int z = (int)(r >> 2), g = (int)(r & 3);
+      const int dst = g < 2 ? g : N + g, src = g < 2 ? N + g : g;
+      const int64_t cb = (int64_t)z * plane + hx + (int64_t)piece * (vec ? VE : 1);
+      rs = cb + (int64_t)src * pitch;
+      rd = cb + (int64_t)dst * pitch;
     }
-    // ghost columns of row (zc, y): -2, -1 <- N-2, N-1 and N, N+1 <- 0, 1
-    const int zc = (int)(u / N), y = (int)(u % N);
-    const int64_t ro = (int64_t)zc * plane + (int64_t)(y + 2) * pitch + hx;
-    if ((N & 1) == 0) {
-      // the column pairs are aligned when N is even
-      const P alo = *reinterpret_cast<const P *>(fa + ro);
-      const P ahi = *reinterpret_cast<const P *>(fa + ro + N - 2);
-      P blo = alo, bhi = ahi;
-      if (two) {
-        blo = *reinterpret_cast<const P *>(fb + ro);
-        bhi = *reinterpret_cast<const P *>(fb + ro + N - 2);
+    uint4 va4 = {}, vb4 = {};
+    E sa = E(0), sb = E(0);
+    if (hr) {
+      if (vec) {
+        va4 = *reinterpret_cast<const uint4 *>(fa + rs);
+        if (two) vb4 = *reinterpret_cast<const uint4 *>(fb + rs);
+      } else {
+        sa = fa[rs];
+        if (two) sb = fb[rs];
       }
-      fa[cb + (int64_t)dst * pitch] = ra;
-      *reinterpret_cast<P *>(fa + ro - 2) = ahi;
-      *reinterpret_cast<P *>(fa + ro + N) = alo;
-      if (two) {
-        fb[cb + (int64_t)dst * pitch] = rb;
-        *reinterpret_cast<P *>(fb + ro - 2) = bhi;
-        *reinterpret_cast<P *>(fb + ro + N) = blo;
-      }
-    } else {
-      E a[4], b[4] = {};
-      const int cs[4] = {0, 1, N - 2, N - 1};
+    }
+    // (a) ghost columns of row (zc, y): -2, -1 <- N-2, N-1 and N, N+1 <- 0, 1
+    const bool hc = u < nc;
+    int64_t ro = 0;
+    E a[4] = {}, b[4] = {};
+    P alo = {}, ahi = {}, blo = {}, bhi = {};
+    if (hc) {
+      const int zc = (int)(u / N), y = (int)(u % N);
+      ro = (int64_t)zc * plane + (int64_t)(y + 2) * pitch + hx;
+      if (even) {
+        alo = *reinterpret_cast<const P *>(fa + ro);
+        ahi = *reinterpret_cast<const P *>(fa + ro + N - 2);
+        if (two) {
+          blo = *reinterpret_cast<const P *>(fb + ro);
+          bhi = *reinterpret_cast<const P *>(fb + ro + N - 2);
+        }
+      } else {
+        const int cs[4] = {0, 1, N - 2, N - 1};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = fa[ro + cs[i]];
-      if (two) {
+        for (int i = 0; i < 4; ++i) a[i] = fa[ro + cs[i]];
+        if (two) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) b[i] = fb[ro + cs[i]];
+          for (int i = 0; i < 4; ++i) b[i] = fb[ro + cs[i]];
+        }
       }
-      fa[cb + (int64_t)dst * pitch] = ra;
-      fa[ro - 2] = a[2]; fa[ro - 1] = a[3]; fa[ro + N] = a[0]; fa[ro + N + 1] = a[1];
-      if (two) {
-        fb[cb + (int64_t)dst * pitch] = rb;
-        fb[ro - 2] = b[2]; fb[ro - 1] = b[3]; fb[ro + N] = b[0]; fb[ro + N + 1] = b[1];
+    }
+    if (hr) {
+      if (vec) {
+        *reinterpret_cast<uint4 *>(fa + rd) = va4;
+        if (two) *reinterpret_cast<uint4 *>(fb + rd) = vb4;
+      } else {
+        fa[rd] = sa;
+        if (two) fb[rd] = sb;
+      }
+    }
+    if (hc) {
+      if (even) {
+        *reinterpret_cast<P *>(fa + ro - 2) = ahi;
+        *reinterpret_cast<P *>(fa + ro + N) = alo;
+        if (two) {
+          *reinterpret_cast<P *>(fb + ro - 2) = bhi;
+          *reinterpret_cast<P *>(fb + ro + N) = blo;
+        }
+      } else {
+        fa[ro - 2] = a[2]; fa[ro - 1] = a[3]; fa[ro + N] = a[0]; fa[ro + N + 1] = a[1];
+        if (two) {
+          fb[ro - 2] = b[2]; fb[ro - 1] = b[3]; fb[ro + N] = b[0]; fb[ro + N + 1] = b[1];
+        }
       }
     }
   }
