@@ -51,8 +51,8 @@ struct PrecFP64 {
   static constexpr bool KAHAN = false;
   static constexpr bool DIFF = false;   // merged-centre stencil (fewest FP64 ops)
   // plane loop unrolled 5 times over a rotating register window (no register
-  // moves) where that measured faster than shifting the window: the FP32 paths
-  // with compensated state or plain (FP64 spills with it, BF16 measured slower)
+  // moves) where that measured faster than shifting the window: the FP32-math
+  // paths (FP64 spills with it)
   static constexpr bool ROTATE = false;
 };
 struct PrecFP32 {
@@ -65,7 +65,7 @@ struct PrecBF16 {
   using TS = float; using TG = __nv_bfloat16; using TM = float;
   static constexpr bool KAHAN = true;
   static constexpr bool DIFF = true;
-  static constexpr bool ROTATE = false;
+  static constexpr bool ROTATE = true;
 };
 struct PrecFP32Plain {
   using TS = float; using TG = float; using TM = float;
