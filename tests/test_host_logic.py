@@ -199,3 +199,31 @@ def test_request_stream_is_seeded_and_in_range():
         n, dt = r.steps()
         h = hi.grid_spacing(r.N, r.L, 0)
         assert dt <= h / 4 + 1e-15 and abs(n * dt - r.T) < 1e-9
+
+
+# ---------------------------------------------------------------- reference arm
+def _ref_args(N=64):
+    import argparse
+    return argparse.Namespace(N=N, steps=1, warmup=3, gpus=1)
+
+
+def test_reference_arm_prints_one_oracle_line(monkeypatch, capsys):
+    """`bench.py --impl reference`: the CPU oracle timed on a slab of the same
+    workload, one JSON line with the contract's keys."""
+    monkeypatch.setenv("RANK", "0")
+    bench.reference_arm(_ref_args())
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["value"] > 0 and line["unit"] == "Gpoint-steps/s"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "Gpoint-steps/s",
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"] == "hbe-512-periodic-grf" and line["config"]["N"] == 64
+
+
+def test_reference_arm_is_silent_on_other_ranks(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    bench.reference_arm(_ref_args())
+    assert capsys.readouterr().out == ""
