@@ -552,6 +552,23 @@ def main():
         "gpu_launches": launches,
     }
 
+    # end to end right after the headline leg, before the other precisions' legs
+    if not args.no_e2e:
+        nsteps = 308 if N == 512 else max(8, int(round(HORIZON / prob.dt)))
+        solves = 3
+        e2e_secs, st, _, phases = e2e_solve(hbe, torch, prob, hbe.FP32, nsteps, solves,
+                                            e2e_bufs)
+        e2e_bufs = None
+        e2e_secs = max_over_ranks(e2e_secs, world, torch, device)
+        line["e2e"] = {"value": float(N) ** 3 * nsteps * solves * world / e2e_secs / 1e9,
+                       "unit": "Gpoint-steps/s",
+                       "h2d_bytes_per_step": 2 * 8 * N ** 3 / nsteps,
+                       "d2h_bytes_per_step": 8 * N ** 3 / nsteps,
+                       "steps_per_solve": nsteps, "solves": solves,
+                       "phases": phases,
+                       "note": "back-to-back solves, each: phi0, phi1 from pinned host, nsteps RK4 "
+                               "steps, phi to pinned host; bytes amortised per RK4 step"}
+
     if not args.no_extra:
         extra = {}
         for name, pid, steps in (("fp64", hbe.FP64, max(10, min(100, args.steps))),
@@ -574,22 +591,6 @@ def main():
                                      "per_point_step": FP64_INSTR_PER_POINT_STEP}
             extra[name] = entry
         line["precisions"] = extra
-
-    if not args.no_e2e:
-        nsteps = 308 if N == 512 else max(8, int(round(HORIZON / prob.dt)))
-        solves = 3
-        e2e_secs, st, _, phases = e2e_solve(hbe, torch, prob, hbe.FP32, nsteps, solves,
-                                            e2e_bufs)
-        e2e_bufs = None
-        e2e_secs = max_over_ranks(e2e_secs, world, torch, device)
-        line["e2e"] = {"value": float(N) ** 3 * nsteps * solves * world / e2e_secs / 1e9,
-                       "unit": "Gpoint-steps/s",
-                       "h2d_bytes_per_step": 2 * 8 * N ** 3 / nsteps,
-                       "d2h_bytes_per_step": 8 * N ** 3 / nsteps,
-                       "steps_per_solve": nsteps, "solves": solves,
-                       "phases": phases,
-                       "note": "back-to-back solves, each: phi0, phi1 from pinned host, nsteps RK4 "
-                               "steps, phi to pinned host; bytes amortised per RK4 step"}
 
     if not args.no_serve:
         line["serve"] = serve_leg(hbe, args.serve_requests)
