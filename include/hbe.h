@@ -213,7 +213,10 @@ hbe_status hbe_load(hbe_ctx *ctx, const char *path);
 const char *hbe_last_error(const hbe_ctx *ctx);
 const char *hbe_status_string(int status);
 
-/* Number of stage-kernel launches this context (or batch) has enqueued. */
+/* Number of stage-kernel launches (and, for a periodic context, ghost-copy
+ * launches) this context (or batch) has enqueued; the two small bookkeeping
+ * kernels of each batch of steps (step coefficients, step advance) are not
+ * counted. */
 int64_t hbe_launch_count(const hbe_ctx *ctx);
 
 /* ---- Radial solutions (Sec. 2.2, Eq. radial) ---------------------------- */
