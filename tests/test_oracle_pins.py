@@ -302,6 +302,127 @@ def test_fd4_weights_are_the_papers(paper_values):
     assert np.count_nonzero(lap) == 13
 
 
+# ---------------------------------------------------------------- P12 zero-Dirichlet wall
+# Eq. (BC) with the 5-wide stencil of Sec. 2.1 needs two ghost layers; the
+# reading taken (C3) is that both hold 0 for every field.  The 1D operator is
+# then the banded N x N matrix of the FD4 weights with the rows simply cut off
+# at the matrix edge, and the 3D operator is its Kronecker sum over the axes.
+# Neither is built from the oracle's own node() rule.
+def _fd4_truncated_matrix(N, h):
+    w = (-1.0 / 12.0, 4.0 / 3.0, -5.0 / 2.0, 4.0 / 3.0, -1.0 / 12.0)
+    D1 = np.zeros((N, N))
+    for i in range(N):
+        for o in range(-2, 3):
+            if 0 <= i + o < N:
+                D1[i, i + o] = w[o + 2] / (h * h)
+    return D1
+
+
+def _kron_laplacian(u, h):
+    """(D x I x I + I x D x I + I x I x D) u for u indexed [z, y, x]."""
+    from scipy import sparse
+    N = u.shape[0]
+    D1 = sparse.csr_matrix(_fd4_truncated_matrix(N, h))
+    I = sparse.identity(N, format="csr")
+    A = (sparse.kron(sparse.kron(I, I), D1) + sparse.kron(sparse.kron(I, D1), I)
+         + sparse.kron(sparse.kron(D1, I), I))
+    return (A @ u.ravel()).reshape(u.shape)
+
+
+def _wall_mismatch(lap):
+    """Largest relative disagreement of `lap(u, h)` with the truncated banded
+    operator: on a random field (all nodes, reported separately for the two
+    layers next to each wall) and on unit spikes at the corner nodes."""
+    N, h = 11, 0.37
+    rng = np.random.default_rng(12)
+    u = rng.standard_normal((N, N, N))
+    got, want = lap(u, h), _kron_laplacian(u, h)
+    scale = np.max(np.abs(want))
+    err = np.max(np.abs(got - want)) / scale
+    wall = [0, 1, N - 2, N - 1]
+    for ax in range(3):
+        sl = [slice(None)] * 3
+        sl[ax] = wall
+        err = max(err, np.max(np.abs(got[tuple(sl)] - want[tuple(sl)])) / scale)
+    # a unit spike on a corner returns the truncated weights: the centre sums
+    # three -5/2 terms, each axis keeps only its inward +1 and +2 neighbours
+    for c in (0, N - 1):
+        e = np.zeros((N, N, N))
+        e[c, c, c] = 1.0
+        g = lap(e, 1.0)
+        s = 1 if c == 0 else -1
+        want_s = np.zeros((N, N, N))
+        want_s[c, c, c] = -7.5
+        for ax in range(3):
+            for o, wgt in ((1, 4.0 / 3.0), (2, -1.0 / 12.0)):
+                idx = [c, c, c]
+                idx[ax] = c + s * o
+                want_s[tuple(idx)] = wgt
+        err = max(err, np.max(np.abs(g - want_s)) / 7.5)
+    return err
+
+
+def test_dirichlet_wall_is_truncated_banded_operator():
+    """The oracle's FD4 Laplacian at and next to the zero-Dirichlet wall equals
+    the banded matrix truncated at the two zero ghost layers (reading C3 of
+    Eq. BC) to rounding."""
+    assert _wall_mismatch(lambda u, h: oracle.laplacian(u, h, D)) <= 1e-13
+
+
+_WALL_RULE = ("  if (i < 0 || i >= g->nx || j < 0 || j >= g->ny || k < 0 || k >= g->nz) "
+              "return 0.0;")
+_WALL_MUTANTS = {
+    # odd reflection about the wall node (index -1): u(-2) = -u(0)
+    "odd_reflection": (
+        "  if (i == -2) return -node(u, g, 0, j, k);\n"
+        "  if (i == g->nx + 1) return -node(u, g, g->nx - 1, j, k);\n"
+        "  if (j == -2) return -node(u, g, i, 0, k);\n"
+        "  if (j == g->ny + 1) return -node(u, g, i, g->ny - 1, k);\n"
+        "  if (k == -2) return -node(u, g, i, j, 0);\n"
+        "  if (k == g->nz + 1) return -node(u, g, i, j, g->nz - 1);\n" + _WALL_RULE),
+    # a single zero ghost layer; the second one mirrors the first interior node
+    "one_ghost_layer": (
+        "  if (i == -2) i = 0;\n  if (i == g->nx + 1) i = g->nx - 1;\n"
+        "  if (j == -2) j = 0;\n  if (j == g->ny + 1) j = g->ny - 1;\n"
+        "  if (k == -2) k = 0;\n  if (k == g->nz + 1) k = g->nz - 1;\n" + _WALL_RULE),
+    # off-by-one bounds: the last interior node read as a ghost
+    "off_by_one_upper": _WALL_RULE.replace("i >= g->nx", "i >= g->nx - 1")
+                                  .replace("j >= g->ny", "j >= g->ny - 1")
+                                  .replace("k >= g->nz", "k >= g->nz - 1"),
+    # off-by-one bounds: the first interior node read as a ghost
+    "off_by_one_lower": _WALL_RULE.replace("i < 0", "i < 1").replace("j < 0", "j < 1")
+                                  .replace("k < 0", "k < 1"),
+}
+
+
+@pytest.mark.parametrize("mutant", sorted(_WALL_MUTANTS))
+def test_dirichlet_wall_pin_rejects_planted_mistakes(mutant, tmp_path):
+    """Plant a plausible wall mistake in a copy of the oracle's C source, build
+    it, and check that the wall pin above rejects it."""
+    import ctypes
+    import subprocess
+    src = open(oracle._SRC).read()
+    assert src.count(_WALL_RULE) == 1
+    path = tmp_path / "mut.c"
+    path.write_text(src.replace(_WALL_RULE, _WALL_MUTANTS[mutant]))
+    so = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", "-o",
+                    str(so), str(path), "-lm"], check=True)
+    lib = ctypes.CDLL(str(so))
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.oracle_laplacian.argtypes = [dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_int]
+    lib.oracle_laplacian.restype = None
+
+    def lap(u, h):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = np.empty_like(u)
+        lib.oracle_laplacian(u.ctypes.data_as(dp), out.ctypes.data_as(dp), u.shape[0], h, D, 1)
+        return out
+
+    assert _wall_mismatch(lap) > 1e-3
+
+
 def test_even_closure_at_origin(paper_values):
     """For data even about a node the FD4 x-derivative there collapses to the
     paper's origin closure (-5/2, 8/3, -1/6) / dr^2 (Sec. 2.2)."""
