@@ -264,25 +264,29 @@ hbe_status hbe_radial_run(int batch, int n, double R, const double *d_mu, const 
 
 /* ---- Stepping without device allocation -------------------------------- */
 /* The paper has no counterpart to this entry point; it serves callers that
- * cannot allocate device memory at the moment they step a problem: code that
- * runs while another library is capturing a CUDA graph on its stream (an
- * allocation there would break or serialise the capture), runtimes that own
- * all device memory through their own pool and forbid other allocations, and
- * real-time loops where cudaMalloc may block or fail under memory pressure.
- * It calls no cudaMalloc, cudaFree or other allocating routine.  The caller
- * passes the initial fields d_phi0, d_phi1 and the result fields d_phi, d_psi
- * (device arrays of N^3 doubles, x fastest); every intermediate array (padded
- * state, stage values, kernel descriptors) lives in one fixed __device__
- * array inside libhbe of about 7.3 MB, which every GPU that loads the library
- * holds until the process exits.  FP64 arithmetic; N in [8, 48], and a larger
- * N returns HBE_EINVAL because the array holds nothing bigger.  Grid,
- * boundary and time conventions as for hbe_create / hbe_step: nsteps RK4
- * steps of size dt from time t0.  The first call on a device looks up the
- * array's device address with that device current, so make that first call
- * before any stream capture.  All calls share the one array (each clears what
- * must start at zero), so calls that overlap on the GPU race.  Runs on
- * `stream` (cudaStream_t, NULL = legacy default) and blocks until done;
- * returns HBE_ETIMEOUT if a kernel's bounded wait expired. */
+ * cannot allocate device memory at the moment they step a problem: runtimes
+ * that own all device memory through their own pool and forbid other
+ * allocations, real-time loops where cudaMalloc may block or fail under
+ * memory pressure, and code that must not grow the device footprint once it
+ * is set up.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ * The caller passes the initial fields d_phi0, d_phi1 and the result fields
+ * d_phi, d_psi (device arrays of N^3 doubles, x fastest); every intermediate
+ * array (padded state, stage values, kernel descriptors) lives in one fixed
+ * __device__ array inside libhbe of 7.33 MB (7,333,888 bytes), which every
+ * GPU that loads the library holds until the process exits.  FP64
+ * arithmetic; N in [8, 48], and a larger N returns HBE_EINVAL because the
+ * array holds nothing bigger.  Grid, boundary and time conventions as for
+ * hbe_create / hbe_step: nsteps RK4 steps of size dt (finite, > 0) from time
+ * t0; nsteps = 0 returns the initial data.  A step whose phi is not finite
+ * ends the solve: the call returns HBE_NONFINITE and the outputs hold the
+ * state after that step (what hbe_read gives after hbe_step reports
+ * HBE_NONFINITE).  The call copies its descriptors from host memory,
+ * synchronises `stream` (cudaStream_t, NULL = legacy default) and blocks
+ * until done, so it must run on a stream that is not being captured into a
+ * CUDA graph.  The first call on a device looks up the array's device address
+ * with that device current.  All calls share the one array (each clears what
+ * must start at zero), so calls that overlap on the GPU race.  Returns
+ * HBE_ETIMEOUT if a kernel's bounded wait expired. */
 hbe_status hbe_step_fp64_noalloc(int N, double L, double mu, double lambda, int bc,
                                  const double *d_phi0, const double *d_phi1, double t0,
                                  double dt, int64_t nsteps, double *d_phi, double *d_psi,

@@ -1,23 +1,25 @@
 // hbe_noalloc.cu -- an RK4 entry point that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc when they want to step a problem: code
-// running while another library captures a CUDA graph on its stream (an
-// allocation there breaks or serialises the capture), runtimes that own all
-// device memory through their own pool and forbid other allocations, and
-// real-time loops where an allocation may block on the driver or fail under
-// memory pressure.  hbe_step_fp64_noalloc serves them: the caller passes the
-// input and output fields (device arrays), and every intermediate array the
-// stage kernels need -- the padded ping-pong state, the three stage
-// right-hand sides, the kernels' descriptor, TMA descriptors, work list and
-// per-step maxima -- lives in one file-scope __device__ array of fixed size,
-// reserved when the library is loaded.  Every GPU that loads libhbe therefore
-// holds kNoAllocScratchBytes (about 7.4 MB) until the process exits.
+// Some callers cannot call cudaMalloc when they want to step a problem:
+// runtimes that own all device memory through their own pool and forbid
+// other allocations, real-time loops where an allocation may block on the
+// driver or fail under memory pressure, and code that must not add to the
+// device's footprint once it is set up.  hbe_step_fp64_noalloc serves them:
+// the caller passes the input and output fields (device arrays), and every
+// intermediate array the stage kernels need -- the padded ping-pong state,
+// the three stage right-hand sides, the kernels' descriptor, TMA descriptors,
+// work list and per-step maxima -- lives in one file-scope __device__ array
+// of fixed size, reserved when the library is loaded.  Every GPU that loads
+// libhbe therefore holds kNoAllocScratchBytes (7,333,888 bytes, 7.33 MB, for
+// N <= 48) until the process exits.
 //
-// The array is shared by every call: each call clears the parts that must
-// start at zero, and two calls that overlap on the GPU (different host
-// threads, or different streams) race on it.  The first call on a device
-// looks up the array's device address (cudaGetSymbolAddress) with that device
-// current; make that first call before any stream capture.
+// The call copies its descriptors from host memory, synchronises the stream
+// and reads the outcome back, so it must be made on a stream that is not
+// being captured into a CUDA graph.  The array is shared by every call: each
+// call clears the parts that must start at zero, and two calls that overlap
+// on the GPU (different host threads, or different streams) race on it.  The
+// first call on a device looks up the array's device address
+// (cudaGetSymbolAddress) with that device current.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -43,6 +45,7 @@ constexpr size_t kFieldBytes =
 constexpr int kFields = 7;  // p0, p1, q0, q1, G1, G2, G3
 constexpr size_t kMetaBytes = 64 * 1024;
 constexpr size_t kNoAllocScratchBytes = kFields * kFieldBytes + kMetaBytes;
+static_assert(kNoAllocScratchBytes == 7333888, "7 fields of 1,038,336 bytes + 64 KiB");
 
 // The scratch.  Host code must not use this name as a pointer: it is a
 // host-side stand-in; the device address comes from cudaGetSymbolAddress.
@@ -114,8 +117,8 @@ extern "C" hbe_status hbe_step_fp64_noalloc(int N, double L, double mu, double l
   if (N < 8 || N > kNoAllocMaxN) return HBE_EINVAL;  // beyond the scratch array's size
   if (!(L > 0.0) || !std::isfinite(L) || !(mu >= 0.0) || !std::isfinite(mu) ||
       !std::isfinite(lambda) || (bc != HBE_BC_DIRICHLET0 && bc != HBE_BC_PERIODIC) ||
-      !d_phi0 || !d_phi1 || !d_phi || !d_psi || !(dt > 0.0) || !std::isfinite(t0) ||
-      nsteps < 0)
+      !d_phi0 || !d_phi1 || !d_phi || !d_psi || !(dt > 0.0) || !std::isfinite(dt) ||
+      !std::isfinite(t0) || nsteps < 0)
     return HBE_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int dev = 0, sms = 0;
@@ -209,11 +212,18 @@ extern "C" hbe_status hbe_step_fp64_noalloc(int N, double L, double mu, double l
     }
     NA_CK(launch_advance(d_desc, d_counts + 1, 1, 1, st));
   }
-  const int set = (int)(nsteps & 1);
-  NA_CK(launch_unpack(0, f[F_P0 + set], nullptr, d_phi, N, pitch, kHX, 0, N, st));
-  NA_CK(launch_unpack(0, f[F_Q0 + set], nullptr, d_psi, N, pitch, kHX, 0, N, st));
+  // where the steps ended: a step whose phi was not finite ends the solve
+  // (the advance kernel sets the status and lets no later step run), so the
+  // last state is that of step n_base, in buffer set n_base & 1
+  Desc out;
   unsigned err = 0;
+  NA_CK(cudaMemcpyAsync(&out, d_desc, sizeof(out), cudaMemcpyDeviceToHost, st));
   NA_CK(cudaMemcpyAsync(&err, d_err, sizeof(err), cudaMemcpyDeviceToHost, st));
   NA_CK(cudaStreamSynchronize(st));
-  return err ? HBE_ETIMEOUT : HBE_OK;
+  if (err) return HBE_ETIMEOUT;
+  const int set = (int)(out.n_base & 1);
+  NA_CK(launch_unpack(0, f[F_P0 + set], nullptr, d_phi, N, pitch, kHX, 0, N, st));
+  NA_CK(launch_unpack(0, f[F_Q0 + set], nullptr, d_psi, N, pitch, kHX, 0, N, st));
+  NA_CK(cudaStreamSynchronize(st));
+  return out.status == ST_NONFINITE ? HBE_NONFINITE : HBE_OK;
 }

@@ -1,0 +1,100 @@
+"""Whole-field parity with the oracle at the full horizon of the benchmark
+workloads.
+
+* Gaussians 256^3 (zero-Dirichlet, mu = sqrt(2), lambda = 1, t in [0, 5], 257
+  RK4 steps of Sec. 2.1): the oracle and the GPU (FP64 and FP32 with
+  compensated state) step side by side to every diagnostic mark (every 0.5
+  time units).  At each mark every node of phi and psi is compared, element
+  by element, with the relative max-norm bounds 1e-11 (FP64) and 2e-5 (FP32),
+  and the GPU's sign masks and component counts are compared bit for bit with
+  the oracle's diagnostics of the same GPU field (bubble definition of
+  Sec. 1).  The oracle resumes each leg from its own state at the previous
+  mark with t0 = m dt, which differs from t0 + m dt of one long run by at most
+  one rounding of t (a relative change of ~1e-16 in e^{-2t}).
+* GRF 512^3 with lambda = 2 at t = 6 (308 steps), where the field breaks into
+  dozens of sign components: the union-find labelling of the GPU against the
+  oracle's breadth-first search on the same field.
+"""
+import numpy as np
+import pytest
+
+import __graft_entry__  # noqa: F401
+import hbe_inputs as hi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+EPS = 1e-6  # sign threshold of the diagnostics (|phi| <= EPS has no sign)
+
+
+@pytest.fixture(scope="module")
+def hbe():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1803_01291_gb300 as m
+    return m
+
+
+def relerr(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def check_diag(s, phi, bc):
+    g = s.diag(eps=EPS, masks=True)
+    o = oracle.diag(phi, bc, eps=EPS)
+    assert np.array_equal(g["pos_mask"], o["pos_mask"])
+    assert np.array_equal(g["neg_mask"], o["neg_mask"])
+    for k in ("n_pos", "n_neg", "bubble_count", "finite"):
+        assert g[k] == o[k], (k, g[k], o[k])
+    assert g["max_abs_phi"] == o["max_abs_phi"]
+    return g["bubble_count"]
+
+
+def test_gaussians_256_whole_field_against_oracle_to_t5(hbe):
+    import torch
+    prob = hi.gaussians_problem(256, seed=0)
+    marks = [int(round(0.5 * j / prob.dt)) for j in range(1, 11)]
+    marks[-1] = prob.nsteps
+    tol = {hbe.FP64: 1e-11, hbe.FP32: 2e-5}
+    solvers = {}
+    try:
+        for prec in tol:
+            s = hbe.Solver(prob.N, prob.L, prob.mu, prob.lam, prob.bc, prec)
+            s.set_initial(torch.from_numpy(prob.phi0).cuda(), torch.from_numpy(prob.phi1).cuda())
+            solvers[prec] = s
+        ophi, opsi = prob.phi0.copy(), prob.phi1.copy()
+        done = 0
+        report = []
+        for m in marks:
+            ophi, opsi, n = oracle.run(ophi, opsi, prob.L, prob.mu, prob.lam, prob.bc,
+                                       done * prob.dt, prob.dt, m - done)
+            assert n == m - done
+            for prec, s in solvers.items():
+                assert s.step(m - done, prob.dt) == hbe.OK
+                phi, psi, t = s.read()
+                assert t == pytest.approx(m * prob.dt, rel=1e-14)
+                ep, eq = relerr(phi, ophi), relerr(psi, opsi)
+                assert ep <= tol[prec], (prec, m, ep)
+                assert eq <= tol[prec], (prec, m, eq)
+                report.append((prec, m, ep, eq, check_diag(s, phi, prob.bc)))
+            done = m
+        print("\n".join(f"prec {p} step {m}: phi {a:.2e} psi {b:.2e} bubbles {c}"
+                        for p, m, a, b, c in report))
+    finally:
+        for s in solvers.values():
+            s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_grf_512_lambda2_components_against_oracle(hbe, prec):
+    import torch
+    prob = hi.grf_problem(512, lam=2.0, seed=0)
+    with hbe.Solver(prob.N, prob.L, prob.mu, prob.lam, prob.bc, prec) as s:
+        s.set_initial(torch.from_numpy(prob.phi0).cuda(), torch.from_numpy(prob.phi1).cuda())
+        assert s.step(prob.nsteps, prob.dt) == hbe.OK
+        phi, _, _ = s.read(psi=False)
+        bubbles = check_diag(s, phi, prob.bc)
+    # the field has broken into many sign components by t = 6
+    assert bubbles >= 10, bubbles
+    torch.cuda.empty_cache()

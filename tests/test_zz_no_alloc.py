@@ -90,3 +90,54 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(env):
     phi0 = np.zeros((N, N, N))
     st, _, _ = noalloc(torch, lib, N, 10.0, 1.0, 1.0, 0, phi0, phi0, 0.0, 0.01, 1)
     assert st == 1  # HBE_EINVAL: the fixed scratch holds N <= 48
+
+
+def test_noalloc_zero_steps_returns_the_initial_data(env):
+    torch, hbe, lib = env
+    N, bc = 20, 1
+    phi0, phi1 = smooth(N, bc, 5)
+    st, phi, psi = noalloc(torch, lib, N, 6.0, 1.0, 1.0, bc, phi0, phi1, 0.0, 0.05, 0)
+    assert st == 0
+    assert np.array_equal(phi, phi0) and np.array_equal(psi, phi1)
+
+
+def test_noalloc_blowup_stops_like_the_allocating_path(env):
+    """Focusing case (lambda < 0) from a large bump: the solve goes non-finite.
+    Both paths return HBE_NONFINITE after the same step and hold the same
+    state; one step fewer is a normal solve equal to the allocating one."""
+    torch, hbe, lib = env
+    N, L, mu, lam, bc = 24, 8.0, 1.0, -1.0, 0
+    h = L / (N + 1)
+    x = (np.arange(N) - (N - 1) / 2) * h
+    r2 = x[None, None, :] ** 2 + x[None, :, None] ** 2 + x[:, None, None] ** 2
+    phi0 = np.where(r2 < 9.0, 30.0 * np.exp(-1.0 / (1.0 - np.minimum(r2, 8.999) / 9.0)), 0.0)
+    phi1 = np.zeros_like(phi0)
+    dt, nsteps = h / 4, 40
+    with hbe.Solver(N, L, mu, lam, bc, hbe.FP64) as s:
+        s.set_initial(phi0, phi1)
+        st_ref = s.step(nsteps, dt)
+        n_stop, _ = s.progress()
+        ref_phi, ref_psi, _ = s.read()
+    assert st_ref == hbe.NONFINITE and 1 <= n_stop < nsteps
+    st, phi, psi = noalloc(torch, lib, N, L, mu, lam, bc, phi0, phi1, 0.0, dt, nsteps)
+    assert st == hbe.NONFINITE
+    for a, b in ((phi, ref_phi), (psi, ref_psi)):
+        fin = np.isfinite(b)
+        assert np.array_equal(np.isfinite(a), fin) and not fin.all()
+        assert np.array_equal(np.isnan(a), np.isnan(b))
+        assert np.array_equal(a[np.isinf(b)], b[np.isinf(b)])
+        if fin.any():
+            assert np.max(np.abs(a[fin] - b[fin])) <= TOL * max(np.max(np.abs(b[fin])), 1e-300)
+    st, phi, psi = noalloc(torch, lib, N, L, mu, lam, bc, phi0, phi1, 0.0, dt, n_stop - 1)
+    assert st == 0
+    ref_phi, ref_psi = allocating(hbe, N, L, mu, lam, bc, phi0, phi1, 0.0, dt, n_stop - 1)
+    assert np.all(np.isfinite(phi))
+    assert relerr(phi, ref_phi) <= TOL and relerr(psi, ref_psi) <= TOL
+
+
+def test_noalloc_rejects_a_non_finite_dt(env):
+    torch, hbe, lib = env
+    N = 16
+    phi0 = np.zeros((N, N, N))
+    st, _, _ = noalloc(torch, lib, N, 10.0, 1.0, 1.0, 0, phi0, phi0, 0.0, float("inf"), 1)
+    assert st == 1
