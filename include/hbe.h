@@ -86,6 +86,12 @@ typedef struct {
   int32_t consumer_warps;
   int32_t smem_bytes[4];    /* dynamic shared memory per stage kernel */
   int32_t ring[4];          /* z-planes in the TMA ring per stage kernel */
+  /* the fused stage-pair kernels (schedule 1): stages 1+2 may use a taller
+   * tile with more consumer warps than the other kernels */
+  int32_t pair_tile_y[2];   /* tile_y of the stages 1+2 and stages 3+4 kernels */
+  int32_t pair_threads[2];
+  int32_t pair_smem_bytes[2];
+  int32_t pair_ring[2];
 } hbe_variant_t;
 
 /* ---- Solver context --------------------------------------------------- */

@@ -46,7 +46,9 @@ class HbeVariant(ctypes.Structure):
                 ("threads", ctypes.c_int32), ("vec", ctypes.c_int32),
                 ("rows_per_warp", ctypes.c_int32), ("consumer_warps", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32 * 4),
-                ("ring", ctypes.c_int32 * 4)]
+                ("ring", ctypes.c_int32 * 4),
+                ("pair_tile_y", ctypes.c_int32 * 2), ("pair_threads", ctypes.c_int32 * 2),
+                ("pair_smem_bytes", ctypes.c_int32 * 2), ("pair_ring", ctypes.c_int32 * 2)]
 
 
 class HBEError(RuntimeError):

@@ -73,6 +73,10 @@ struct hbe_ctx {
   int *d_nitems = nullptr;
   int *d_one = nullptr;
   int nitems = 0, items_cap = 0;
+  // work list of the stages 1+2 kernel, whose tile may differ from the others'
+  WorkItem *d_items_p = nullptr;
+  int *d_nitems_p = nullptr;
+  int nitems_p = 0, items_cap_p = 0, zchunk_p = 0;
   int grid[6] = {0, 0, 0, 0, 0, 0};
   int schedule = 1;  // 0: four one-stage kernels per step; 1: two fused stage pairs
   unsigned *d_err = nullptr;
@@ -106,7 +110,7 @@ struct hbe_batch {
     int *d_n = nullptr;
     int cap = 0;
     int grid[6] = {0, 0, 0, 0, 0, 0};
-  } lists[kMaxVariants];
+  } lists[kMaxVariants], lists_p[kMaxVariants];  // lists_p: the stages 1+2 kernel's tiles
   int nvariants = 0;
   unsigned *d_err = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -203,10 +207,12 @@ int auto_zchunk(int N, int columns, int resident) {
   return best_zc;
 }
 
-// Work items of one context, ordered z-chunk, then y, then x (neighbouring
-// tiles run together, so halo rows are still in L2 when they are read).
-void build_items(const hbe_ctx *ctx, int member, int zchunk, std::vector<WorkItem> &out) {
-  const KernelInfo &ki = table_for(ctx->prec).k[ctx->variant][0];
+// Work items of one context for the tile of stage kernel `kidx` (0: the
+// tile of every kernel but the stages 1+2 one, 4: that kernel's), ordered
+// z-chunk, then y, then x (neighbouring tiles run together, so halo rows are
+// still in L2 when they are read).
+void build_items(const hbe_ctx *ctx, int member, int zchunk, int kidx, std::vector<WorkItem> &out) {
+  const KernelInfo &ki = table_for(ctx->prec).k[ctx->variant][kidx];
   const int tx = (ctx->N + ki.tx - 1) / ki.tx, ty = (ctx->N + ki.ty - 1) / ki.ty;
   for (int z0 = 0; z0 < ctx->N; z0 += zchunk)
     for (int j = 0; j < ty; ++j)
@@ -247,33 +253,53 @@ hbe_status apply_tuning(hbe_ctx *ctx, int variant, int zchunk) {
   if ((st = E(TM_G2_H, F_G2, eg, ctx->pitch_g, bxg, by))) return st;
   if ((st = E(TM_G2_I, F_G2, eg, ctx->pitch_g, tx, ty))) return st;
   if ((st = E(TM_G3_I, F_G3, eg, ctx->pitch_g, tx, ty))) return st;
+  // halo boxes of p and q for the stages 1+2 kernel's own tile
+  const int txp = ks[4].tx, typ = ks[4].ty;
+  if ((st = E(TM_P_H0_P, F_P0, es, ctx->pitch_s, txp + 2 * ctx->hxs, typ + 4))) return st;
+  if ((st = E(TM_P_H1_P, F_P1, es, ctx->pitch_s, txp + 2 * ctx->hxs, typ + 4))) return st;
+  if ((st = E(TM_Q_H0_P, F_Q0, es, ctx->pitch_s, txp + 2 * ctx->hxs, typ + 4))) return st;
+  if ((st = E(TM_Q_H1_P, F_Q1, es, ctx->pitch_s, txp + 2 * ctx->hxs, typ + 4))) return st;
   CK(cudaMemcpy(ctx->d_tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice));
-  // persistent grid per stage and the work list
+  // persistent grid per stage and the two work lists
   int resident = 1 << 30;
   for (int s = 0; s < 6; ++s) {
     if ((st = persistent_grid(ctx->err, ks[s], ctx->sms, &ctx->grid[s]))) return st;
-    resident = std::min(resident, ctx->grid[s]);
+    if (s != 4) resident = std::min(resident, ctx->grid[s]);
   }
   const int columns = ((ctx->N + tx - 1) / tx) * ((ctx->N + ty - 1) / ty);
+  const int columns_p = ((ctx->N + txp - 1) / txp) * ((ctx->N + typ - 1) / typ);
   ctx->zchunk = zchunk > 0 ? std::min(zchunk, ctx->N) : auto_zchunk(ctx->N, columns, resident);
-  std::vector<WorkItem> items;
-  build_items(ctx, 0, ctx->zchunk, items);
-  if ((int)items.size() > ctx->items_cap) {
-    if (ctx->d_items) cudaFree(ctx->d_items);
-    ctx->d_items = nullptr;
-    CK(cudaMalloc(&ctx->d_items, items.size() * sizeof(WorkItem)));
-    ctx->items_cap = (int)items.size();
+  ctx->zchunk_p =
+      zchunk > 0 ? std::min(zchunk, ctx->N) : auto_zchunk(ctx->N, columns_p, ctx->grid[4]);
+  for (int li = 0; li < 2; ++li) {
+    std::vector<WorkItem> items;
+    build_items(ctx, 0, li ? ctx->zchunk_p : ctx->zchunk, li ? 4 : 0, items);
+    WorkItem *&d_items = li ? ctx->d_items_p : ctx->d_items;
+    int &cap = li ? ctx->items_cap_p : ctx->items_cap;
+    int &n = li ? ctx->nitems_p : ctx->nitems;
+    if ((int)items.size() > cap) {
+      if (d_items) cudaFree(d_items);
+      d_items = nullptr;
+      CK(cudaMalloc(&d_items, items.size() * sizeof(WorkItem)));
+      cap = (int)items.size();
+    }
+    n = (int)items.size();
+    CK(cudaMemcpy(d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(li ? ctx->d_nitems_p : ctx->d_nitems, &n, sizeof(int), cudaMemcpyHostToDevice));
   }
-  ctx->nitems = (int)items.size();
-  CK(cudaMemcpy(ctx->d_items, items.data(), items.size() * sizeof(WorkItem),
-                cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->d_nitems, &ctx->nitems, sizeof(int), cudaMemcpyHostToDevice));
-  for (int s = 0; s < 6; ++s) ctx->grid[s] = std::min(ctx->grid[s], ctx->nitems);
+  for (int s = 0; s < 6; ++s)
+    ctx->grid[s] = std::min(ctx->grid[s], s == 4 ? ctx->nitems_p : ctx->nitems);
   if (ctx->gexec) {
     cudaGraphExecDestroy(ctx->gexec);
     ctx->gexec = nullptr;
   }
   return HBE_OK;
+}
+
+// Parameters of stage kernel s (0..5) of a context for step k of a graph replay.
+StageParams ctx_params(const hbe_ctx *ctx, int s, int k) {
+  return StageParams{ctx->d_desc, s == 4 ? ctx->d_items_p : ctx->d_items,
+                     s == 4 ? ctx->d_nitems_p : ctx->d_nitems, ctx->d_err, k};
 }
 
 hbe_status launch_stage(std::string &err, const KernelInfo &ki, int grid, const StageParams &p,
@@ -326,8 +352,8 @@ hbe_status ensure_graph(hbe_ctx *ctx) {
   if (ec != cudaSuccess) st = set_err(ctx->err, HBE_ECUDA, "%s", cudaGetErrorString(ec));
   for (int k = 0; k < ctx->K && st == HBE_OK; ++k)
     for (int s = first; s < last && st == HBE_OK; ++s) {
-      StageParams p{ctx->d_desc, ctx->d_items, ctx->d_nitems, ctx->d_err, k};
-      st = launch_stage(ctx->err, vt.k[ctx->variant][s], ctx->grid[s], p, ctx->cap_stream);
+      st = launch_stage(ctx->err, vt.k[ctx->variant][s], ctx->grid[s], ctx_params(ctx, s, k),
+                        ctx->cap_stream);
       if (st == HBE_OK && ctx->bc == HBE_BC_PERIODIC && stage_needs_wrap(s + 1)) {
         cudaError_t ew = launch_wrap(ctx->d_desc, ctx->d_one, 1, k, s + 1, wrap_blocks(ctx),
                                      ctx->cap_stream);
@@ -503,6 +529,7 @@ hbe_status create_common(int N, double L, double mu, double lambda, int bc, int 
   CKB(cudaMalloc(&ctx->d_desc, sizeof(Desc)));
   CKB(cudaMallocHost(&ctx->h_desc, sizeof(Desc)));
   CKB(cudaMalloc(&ctx->d_nitems, sizeof(int)));
+  CKB(cudaMalloc(&ctx->d_nitems_p, sizeof(int)));
   CKB(cudaMalloc(&ctx->d_one, sizeof(int)));
   CKB(cudaMalloc(&ctx->d_err, sizeof(unsigned)));
   CKB(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
@@ -571,6 +598,8 @@ void hbe_destroy(hbe_ctx *ctx) {
   if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
   cudaFree(ctx->d_items);
   cudaFree(ctx->d_nitems);
+  cudaFree(ctx->d_items_p);
+  cudaFree(ctx->d_nitems_p);
   cudaFree(ctx->d_one);
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_stage);
@@ -616,6 +645,12 @@ hbe_status hbe_variant_info(int prec, int variant, hbe_variant_t *out) {
   for (int s = 0; s < 4; ++s) {
     out->smem_bytes[s] = k[s].smem;
     out->ring[s] = k[s].ring;
+  }
+  for (int i = 0; i < 2; ++i) {
+    out->pair_tile_y[i] = k[4 + i].ty;
+    out->pair_threads[i] = k[4 + i].threads;
+    out->pair_smem_bytes[i] = k[4 + i].smem;
+    out->pair_ring[i] = k[4 + i].ring;
   }
   return HBE_OK;
 }
@@ -865,9 +900,8 @@ hbe_status hbe_profile_stages(hbe_ctx *ctx, int64_t nsteps, double dt, float *ms
     CK(launch_coef(ctx->d_desc, ctx->d_one, 1, 1, ctx->stream));
     for (int s = 0; s < nl && st == HBE_OK; ++s) {
       CK(cudaEventRecord(ev[(n * nl + s) * 2], ctx->stream));
-      StageParams p{ctx->d_desc, ctx->d_items, ctx->d_nitems, ctx->d_err, 0};
-      st = launch_stage(ctx->err, vt.k[ctx->variant][first + s], ctx->grid[first + s], p,
-                        ctx->stream);
+      st = launch_stage(ctx->err, vt.k[ctx->variant][first + s], ctx->grid[first + s],
+                        ctx_params(ctx, first + s, 0), ctx->stream);
       CK(cudaEventRecord(ev[(n * nl + s) * 2 + 1], ctx->stream));
       if (st == HBE_OK && ctx->bc == HBE_BC_PERIODIC && stage_needs_wrap(first + s + 1)) {
         CK(launch_wrap(ctx->d_desc, ctx->d_one, 1, 0, first + s + 1, wrap_blocks(ctx), ctx->stream));
@@ -1156,10 +1190,11 @@ void hbe_batch_destroy(hbe_batch *b) {
   cudaFree(b->d_descs);
   if (b->h_descs) cudaFreeHost(b->h_descs);
   cudaFree(b->d_ndesc);
-  for (auto &l : b->lists) {
-    cudaFree(l.d_items);
-    cudaFree(l.d_n);
-  }
+  for (auto *ls : {b->lists, b->lists_p})
+    for (int v = 0; v < kMaxVariants; ++v) {
+      cudaFree(ls[v].d_items);
+      cudaFree(ls[v].d_n);
+    }
   cudaFree(b->d_err);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   delete b;
@@ -1226,16 +1261,18 @@ static hbe_status batch_rebuild(hbe_batch *b) {
     b->cap_desc = cap;
     recapture = true;
   }
-  std::vector<WorkItem> items[kMaxVariants];
+  std::vector<WorkItem> items[2][kMaxVariants];
   for (int i = 0; i < M; ++i) {
     hbe_ctx *c = b->members[i];
     b->h_descs[i] = *c->h_desc;
-    build_items(c, i, c->zchunk, items[c->variant]);
+    build_items(c, i, c->zchunk, 0, items[0][c->variant]);
+    build_items(c, i, c->zchunk_p, 4, items[1][c->variant]);
   }
   const VariantTable &vt = table_for(b->prec);
-  for (int v = 0; v < b->nvariants; ++v) {
-    auto &l = b->lists[v];
-    const int n = (int)items[v].size();
+  for (int lv = 0; lv < 2 * b->nvariants; ++lv) {
+    const int li = lv / b->nvariants, v = lv % b->nvariants;
+    auto &l = li ? b->lists_p[v] : b->lists[v];
+    const int n = (int)items[li][v].size();
     if (n > l.cap || !l.d_n) {
       int cap = std::max(4096, l.cap);
       while (cap < n) cap *= 2;
@@ -1251,7 +1288,7 @@ static hbe_status batch_rebuild(hbe_batch *b) {
       recapture = true;
     }
     if (n)
-      CKX(b->err, cudaMemcpyAsync(l.d_items, items[v].data(), n * sizeof(WorkItem),
+      CKX(b->err, cudaMemcpyAsync(l.d_items, items[li][v].data(), n * sizeof(WorkItem),
                                   cudaMemcpyHostToDevice, b->stream));
     CKX(b->err, cudaMemcpyAsync(l.d_n, &n, sizeof(int), cudaMemcpyHostToDevice, b->stream));
     CKX(b->err, cudaStreamSynchronize(b->stream));  // n lives on this stack frame
@@ -1272,7 +1309,7 @@ static hbe_status batch_rebuild(hbe_batch *b) {
     for (int k = 0; k < b->K && st == HBE_OK; ++k)
       for (int s = 4; s < 6 && st == HBE_OK; ++s) {
         for (int v = 0; v < b->nvariants && st == HBE_OK; ++v) {
-          auto &l = b->lists[v];
+          auto &l = s == 4 ? b->lists_p[v] : b->lists[v];
           if (!l.d_n) continue;
           StageParams p{b->d_descs, l.d_items, l.d_n, b->d_err, k};
           st = launch_stage(b->err, vt.k[v][s], l.grid[s], p, b->cap_stream);

@@ -26,10 +26,13 @@ enum Field : int {
 };
 
 // TMA descriptors of one context: halo boxes (tile + 2 rows / HX columns of
-// ghost on each side) and interior boxes (the tile only).
+// ghost on each side) and interior boxes (the tile only).  The stages 1+2
+// kernel may use a taller tile than the others; its halo boxes of p and q are
+// the *_P maps (the same boxes as TM_P_H* / TM_Q_H* when the tiles agree).
 enum TMap : int {
   TM_P_H0 = 0, TM_P_H1, TM_Q_H0, TM_Q_H1, TM_Q_I0, TM_Q_I1, TM_PLO_I0, TM_PLO_I1,
-  TM_QLO_I0, TM_QLO_I1, TM_G1_H, TM_G1_I, TM_G2_H, TM_G2_I, TM_G3_I, NUM_TMAPS
+  TM_QLO_I0, TM_QLO_I1, TM_G1_H, TM_G1_I, TM_G2_H, TM_G2_I, TM_G3_I,
+  TM_P_H0_P, TM_P_H1_P, TM_Q_H0_P, TM_Q_H1_P, NUM_TMAPS
 };
 
 enum DevError : unsigned { DEV_ERR_TIMEOUT = 1u, DEV_ERR_UNIONFIND = 2u };

@@ -124,6 +124,16 @@ struct StageCfg {
   static constexpr bool ROTATE = PR::ROTATE;
   // packed FP32 arithmetic for pairs of x points (FP32 math, even VEC, difference form)
   static constexpr bool PACKED = sizeof(TM) == 4 && VEC % 2 == 0 && DIFF;
+  // one row per warp with packed arithmetic: the 13-point sums are formed part
+  // by part (z pairs, rows +-1, rows +-2, x pairs), so fewer neighbour values
+  // are live at once
+  static constexpr bool INCR = PACKED && VY_ == 1 && S_ == 5;
+  // stages 1+2: the x neighbours of both stage arguments are formed from the
+  // ring's halo columns by every lane instead of exchanged by warp shuffles
+  static constexpr bool XLDS = PACKED && S_ == 5;
+  // stage arguments formed by packed FMAs (stages 1+2; the stages 3+4 kernel,
+  // which holds the compensated state, spills with them)
+  static constexpr bool PCOMB = PACKED && S_ == 5;
   static_assert(VEC == 1 || VEC == 2 || VEC == 4, "1, 2 or 4 x points per lane");
   static_assert(VEC * (int)sizeof(TM) <= 16, "lane vector of <= 16 bytes");
   static_assert(HXS >= 2 && HXG >= 2 && HXS % VEC == 0 && HXG % VEC == 0, "halo alignment");
@@ -299,8 +309,8 @@ __device__ __forceinline__ void produce(const StageParams &prm, uint64_t *full, 
     const int N = d->N;
     const bool periodic = d->bc == 1;
     const int set = (int)((d->n_base + prm.k) & 1);
-    const CUtensorMap *mp = tm + (set ? TM_P_H1 : TM_P_H0);
-    const CUtensorMap *mq = tm + (set ? TM_Q_H1 : TM_Q_H0);
+    const CUtensorMap *mp = tm + (S == 5 ? (set ? TM_P_H1_P : TM_P_H0_P) : (set ? TM_P_H1 : TM_P_H0));
+    const CUtensorMap *mq = tm + (S == 5 ? (set ? TM_Q_H1_P : TM_Q_H0_P) : (set ? TM_Q_H1 : TM_Q_H0));
     const CUtensorMap *mg = tm + (S == 3 ? TM_G1_H : TM_G2_H);
     const CUtensorMap *mi0 = tm + (S == 1 ? (set ? TM_Q_I1 : TM_Q_I0)
                                           : (S == 2 ? TM_G1_I : (S == 3 ? TM_G2_I : TM_G1_I)));
@@ -435,6 +445,16 @@ __device__ __forceinline__ TM lap_g(TM c43, TM cm12, TM ccen, TM nlam, TM m3, bo
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
 }
+// The reaction and damping terms and the weighted pair sums s1 (distance 1)
+// and s2 (distance 2) of the difference-form stencil, on two points at once.
+__device__ __forceinline__ float2 lap_tail2(float2 c43, float2 cm12, float2 ccen, float2 nlam,
+                                           float2 m3, float2 P0, float2 s1, float2 s2,
+                                           float2 Q) {
+  float2 g = __ffma2_rn(__fmul2_rn(nlam, __fmul2_rn(P0, P0)), P0, __fmul2_rn(m3, Q));
+  g = __ffma2_rn(ccen, P0, g);
+  g = __ffma2_rn(cm12, s2, g);
+  return __ffma2_rn(c43, s1, g);
+}
 __device__ __forceinline__ float2 lap_g2(float2 c43, float2 cm12, float2 ccen, float2 nlam,
                                          float2 m3, float2 P0, float2 xm2, float2 xm1,
                                          float2 xp1, float2 xp2, float2 ym2, float2 ym1,
@@ -446,10 +466,7 @@ __device__ __forceinline__ float2 lap_g2(float2 c43, float2 cm12, float2 ccen, f
   const float2 s2 = __fadd2_rn(__fadd2_rn(sub2(xm2, P0), sub2(xp2, P0)),
                                __fadd2_rn(__fadd2_rn(sub2(ym2, P0), sub2(yp2, P0)),
                                           __fadd2_rn(sub2(zm2, P0), sub2(zp2, P0))));
-  float2 g = __ffma2_rn(__fmul2_rn(nlam, __fmul2_rn(P0, P0)), P0, __fmul2_rn(m3, Q));
-  g = __ffma2_rn(ccen, P0, g);
-  g = __ffma2_rn(cm12, s2, g);
-  return __ffma2_rn(c43, s1, g);
+  return lap_tail2(c43, cm12, ccen, nlam, m3, P0, s1, s2, Q);
 }
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
@@ -490,12 +507,24 @@ struct Consumer {
       if (gtile(kk) >= 0)
         load_as<TG, TM, n>(reinterpret_cast<const TG *>(base + C::OFF_HG + gtile(kk) * C::HG_BYTES) +
                                (ly + 2) * BXG + lx + HXG, gv);
+      if constexpr (C::PCOMB && n % 2 == 0) {
+        // pairs of points per packed FMA (each element rounded as fmaf)
 #pragma unroll
-      for (int j = 0; j < n; ++j) {
-        TM v = pv[j];
-        if (uses_q(kk)) v = fmaT(k.kq[kk], qv[j], v);
-        if (gtile(kk) >= 0) v = fmaT(k.kg[kk], gv[j], v);
-        out[kk][j] = v;
+        for (int j = 0; j < n; j += 2) {
+          float2 v = f2(pv[j], pv[j + 1]);
+          if (uses_q(kk)) v = __ffma2_rn(f2(k.kq[kk]), f2(qv[j], qv[j + 1]), v);
+          if (gtile(kk) >= 0) v = __ffma2_rn(f2(k.kg[kk]), f2(gv[j], gv[j + 1]), v);
+          out[kk][j] = v.x;
+          out[kk][j + 1] = v.y;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+          TM v = pv[j];
+          if (uses_q(kk)) v = fmaT(k.kq[kk], qv[j], v);
+          if (gtile(kk) >= 0) v = fmaT(k.kg[kk], gv[j], v);
+          out[kk][j] = v;
+        }
       }
     }
   }
@@ -508,7 +537,18 @@ struct Consumer {
     for (int kk = 0; kk < KN; ++kk)
 #pragma unroll
       for (int j = 0; j < VEC; ++j) e[kk][2 + j] = c[kk][j];
-    if constexpr (S == 1) {
+    if constexpr (C::XLDS) {
+      // every lane forms its four x neighbours of each kind from the halo
+      // columns of the ring tiles (the same values the neighbouring lanes hold)
+      TM l[KN][2], rr[KN][2];
+      comb<2>(base, lx0 - 2, ly, l);
+      comb<2>(base, lx0 + VEC, ly, rr);
+#pragma unroll
+      for (int kk = 0; kk < KN; ++kk) {
+        e[kk][0] = l[kk][0]; e[kk][1] = l[kk][1];
+        e[kk][VEC + 2] = rr[kk][0]; e[kk][VEC + 3] = rr[kk][1];
+      }
+    } else if constexpr (S == 1) {
       // P = p: neighbours straight from the halo tile
       const TS *hp = reinterpret_cast<const TS *>(base) + (ly + 2) * BXS + lx0 + HXS;
       if constexpr (VEC >= 2) {
@@ -605,8 +645,8 @@ struct Consumer {
     // z = W(m-2), z+1 = W(m-1), z+2 = W(m))
     const int z = it.z0 + m - 4;
     const unsigned char *b2 = ring + s2 * C::SLOT_BYTES;
-    TM R[KN][4][VEC];  // rows ly0-2, ly0-1, ly0+VY, ly0+VY+1 of P at plane z
-    {
+    TM R[KN][4][VEC];  // rows ly0-2, ly0-1, ly0+VY, ly0+VY+1 of P at plane z (not INCR)
+    if constexpr (!C::INCR) {
       TM t[KN][VEC];
       const int rows[4] = {ly0 - 2, ly0 - 1, ly0 + VY, ly0 + VY + 1};
 #pragma unroll
@@ -632,7 +672,7 @@ struct Consumer {
 #pragma unroll
         for (int j = 0; j < VEC; ++j) c[kk][j] = win[WM2][kk][r][j];
       TM e[KN][VEC + 4];
-      xnb(b2, ly, c, e);
+      if constexpr (!C::INCR) xnb(b2, ly, c, e);
       const int hoff = (ly + 2) * BXS + lx0 + HXS;
       const int ioff = ly * TX + lx0;
       // point-only values of plane z
@@ -666,7 +706,63 @@ struct Consumer {
         load_as<TS, TM, VEC>(is + C::IS_BYTES / (int)sizeof(TS), lq);
       }
       TM res[KN][VEC];
-      if constexpr (C::PACKED) {
+      if constexpr (C::INCR) {
+        // the pair sums of lap_g2 in its association, formed part by part:
+        // s1 = x1 + (y1 + z1), s2 = x2 + (y2 + z2)
+        constexpr int NP = VEC / 2;
+        float2 P0[KN][NP], A1[KN][NP], A2[KN][NP];
+#pragma unroll
+        for (int kk = 0; kk < KN; ++kk)
+#pragma unroll
+          for (int jp = 0; jp < NP; ++jp) {
+            const int j = 2 * jp;
+            P0[kk][jp] = f2(c[kk][j], c[kk][j + 1]);
+            A1[kk][jp] = __fadd2_rn(sub2(f2(win[WM3][kk][0][j], win[WM3][kk][0][j + 1]), P0[kk][jp]),
+                                    sub2(f2(win[WM1][kk][0][j], win[WM1][kk][0][j + 1]), P0[kk][jp]));
+            A2[kk][jp] = __fadd2_rn(sub2(f2(win[WM4][kk][0][j], win[WM4][kk][0][j + 1]), P0[kk][jp]),
+                                    sub2(f2(win[W0][kk][0][j], win[W0][kk][0][j + 1]), P0[kk][jp]));
+          }
+#pragma unroll
+        for (int d = 1; d <= 2; ++d) {
+          TM a[KN][VEC], b[KN][VEC];
+          comb<VEC>(b2, lx0, ly - d, a);
+          comb<VEC>(b2, lx0, ly + d, b);
+#pragma unroll
+          for (int kk = 0; kk < KN; ++kk)
+#pragma unroll
+            for (int jp = 0; jp < NP; ++jp) {
+              const int j = 2 * jp;
+              const float2 yy = __fadd2_rn(sub2(f2(a[kk][j], a[kk][j + 1]), P0[kk][jp]),
+                                           sub2(f2(b[kk][j], b[kk][j + 1]), P0[kk][jp]));
+              if (d == 1) A1[kk][jp] = __fadd2_rn(yy, A1[kk][jp]);
+              else A2[kk][jp] = __fadd2_rn(yy, A2[kk][jp]);
+            }
+        }
+        xnb(b2, ly, c, e);
+#pragma unroll
+        for (int kk = 0; kk < KN; ++kk) {
+#pragma unroll
+          for (int jp = 0; jp < NP; ++jp) {
+            const int j = 2 * jp;
+            const float2 s1 = __fadd2_rn(__fadd2_rn(sub2(f2(e[kk][j + 1], e[kk][j + 2]), P0[kk][jp]),
+                                                    sub2(f2(e[kk][j + 3], e[kk][j + 4]), P0[kk][jp])),
+                                         A1[kk][jp]);
+            const float2 s2 = __fadd2_rn(__fadd2_rn(sub2(f2(e[kk][j], e[kk][j + 1]), P0[kk][jp]),
+                                                    sub2(f2(e[kk][j + 4], e[kk][j + 5]), P0[kk][jp])),
+                                         A2[kk][jp]);
+            float2 Q;
+            if (kk == 0)
+              Q = (S == 1 || S == 5) ? f2(qS[j], qS[j + 1])
+                                     : __ffma2_rn(f2(k.q0), f2(X[j], X[j + 1]), f2(qS[j], qS[j + 1]));
+            else
+              Q = __ffma2_rn(f2(k.q1), f2(res[0][j], res[0][j + 1]), f2(qS[j], qS[j + 1]));
+            const float2 g = lap_tail2(f2(k.c43[kk]), f2(k.cm12[kk]), f2(k.ccen[kk]), f2(k.nlam),
+                                       f2(k.m3), P0[kk][jp], s1, s2, Q);
+            res[kk][j] = g.x;
+            res[kk][j + 1] = g.y;
+          }
+        }
+      } else if constexpr (C::PACKED) {
         // two x points per packed instruction (bitwise the scalar results)
 #pragma unroll
         for (int kk = 0; kk < KN; ++kk) {

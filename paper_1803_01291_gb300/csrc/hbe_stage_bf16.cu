@@ -9,14 +9,15 @@ KernelInfo info() {
   return KernelInfo{reinterpret_cast<const void *>(&stage_kernel<C>), C::THREADS, C::SMEM, C::RING,
                     C::TX, C::TY, C::VEC, C::VY, C::NW};
 }
-template <class PR, int V, int VY, int NW, int B, int MB>
+// NW5: consumer warps of the stages 1+2 kernel (its tile is 32 V x NW5 VY)
+template <class PR, int V, int VY, int NW, int B, int MB, int NW5 = NW>
 void add(VariantTable &t) {
   KernelInfo *k = t.k[t.count++];
   k[0] = info<StageCfg<PR, V, VY, NW, B, MB, 1>>();
   k[1] = info<StageCfg<PR, V, VY, NW, B, MB, 2>>();
   k[2] = info<StageCfg<PR, V, VY, NW, B, MB, 3>>();
   k[3] = info<StageCfg<PR, V, VY, NW, B, MB, 4>>();
-  k[4] = info<StageCfg<PR, V, VY, NW, B, MB, 5>>();
+  k[4] = info<StageCfg<PR, V, VY, NW5, B, MB, 5>>();
   k[5] = info<StageCfg<PR, V, VY, NW, B, MB, 6>>();
 }
 }  // namespace
@@ -26,6 +27,9 @@ const VariantTable &variants_bf16() {
     using PR = PrecBF16;
     VariantTable t{};
     // <precision, x points per lane, rows per warp, consumer warps, smem budget, min blocks/SM>
+    // 128 x 11 tile, 12 warps, one CTA per SM; stages 1+2 on a 128 x 15 tile,
+    // 16 warps at <= 128 registers
+    add<PR, 4, 1, 11, 220 * 1024, 1, 15>(t);
     add<PR, 4, 1, 11, 220 * 1024, 1>(t);  // 128 x 11 tile, 12 warps, one CTA per SM
     add<PR, 4, 1, 8, 220 * 1024, 1>(t);   // 128 x 8 tile, 9 warps, one CTA per SM
     add<PR, 2, 1, 11, 220 * 1024, 1>(t);  // 64 x 11 tile, 12 warps, one CTA per SM

@@ -14,11 +14,12 @@ struct KernelInfo {
   int nw;           // consumer warps
 };
 
-constexpr int kMaxVariants = 4;
+constexpr int kMaxVariants = 6;
 
 struct VariantTable {
   int count;
-  // [variant][0..3] one RK stage per launch; [4] stages 1+2; [5] stages 3+4 + combine
+  // [variant][0..3] one RK stage per launch; [4] stages 1+2; [5] stages 3+4 + combine.
+  // Every kernel of a variant has the same tile except [4], which may be taller.
   KernelInfo k[kMaxVariants][6];
 };
 

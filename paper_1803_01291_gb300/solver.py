@@ -49,7 +49,9 @@ def variants(prec: int) -> List[dict]:
         _check(lib, lib.hbe_variant_info(prec, v, ctypes.byref(info)))
         out.append(dict(tile_x=info.tile_x, tile_y=info.tile_y, threads=info.threads, vec=info.vec,
                         rows_per_warp=info.rows_per_warp, consumer_warps=info.consumer_warps,
-                        smem=list(info.smem_bytes), ring=list(info.ring)))
+                        smem=list(info.smem_bytes), ring=list(info.ring),
+                        pair_tile_y=list(info.pair_tile_y), pair_threads=list(info.pair_threads),
+                        pair_smem=list(info.pair_smem_bytes), pair_ring=list(info.pair_ring)))
     return out
 
 
