@@ -133,7 +133,11 @@ hbe_status hbe_variant_info(int prec, int variant, hbe_variant_t *out);
 hbe_status hbe_set_schedule(hbe_ctx *ctx, int schedule);
 int hbe_variant_count(int prec);
 
-/* Initial data (Eq. HBEinit) at time t0: host arrays of N^3 doubles, copied. */
+/* Initial data (Eq. HBEinit) at time t0: host arrays of N^3 doubles, copied.
+ * Page-locked host arrays (cudaMallocHost / cudaHostRegister) are read by the
+ * packing kernel directly over the host link; pageable arrays go through
+ * device staging buffers with asynchronous copies.  Returns when the data is
+ * on the device. */
 hbe_status hbe_set_initial(hbe_ctx *ctx, const double *phi0, const double *phi1, double t0);
 /* Same from device arrays (read on the context's stream before return). */
 hbe_status hbe_set_initial_device(hbe_ctx *ctx, const double *d_phi0, const double *d_phi1,
@@ -166,7 +170,9 @@ hbe_status hbe_step(hbe_ctx *ctx, int64_t nsteps, double dt);
 hbe_status hbe_step_async(hbe_ctx *ctx, int64_t nsteps, double dt);
 hbe_status hbe_sync(hbe_ctx *ctx);
 
-/* Current state to host arrays of N^3 doubles (psi may be NULL) and time. */
+/* Current state to host arrays of N^3 doubles (psi may be NULL) and time.
+ * Page-locked host arrays are written by the unpacking kernel directly;
+ * pageable arrays receive the data through device staging buffers. */
 hbe_status hbe_read(hbe_ctx *ctx, double *phi, double *psi, double *t);
 /* Same to device arrays on the context's stream (not synchronised). */
 hbe_status hbe_read_device(hbe_ctx *ctx, double *d_phi, double *d_psi);

@@ -312,6 +312,20 @@ hbe_status launch_stage(std::string &err, const KernelInfo &ki, int grid, const 
 
 // Debug mode: periodic contexts start with NaN bit patterns in every field
 // (HBE_DEBUG_NAN_GHOSTS set and not "0"), read at each context creation.
+// Device-side address of a host buffer the GPU can read and write directly
+// (page-locked memory: cudaMallocHost, cudaHostAlloc or cudaHostRegister), or
+// nullptr for pageable memory.  On a Grace host such a buffer is reached over
+// NVLink-C2C by ordinary loads and stores, so the pack / unpack kernels can
+// move the fields without the copy engines or a staging buffer.
+const void *pinned_device_ptr(const void *host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 bool nan_canary(const hbe_ctx *ctx) {
   if (ctx->bc != HBE_BC_PERIODIC) return false;
   const char *v = std::getenv("HBE_DEBUG_NAN_GHOSTS");
@@ -692,11 +706,15 @@ static hbe_status set_initial_impl(hbe_ctx *ctx, const double *phi0, const doubl
   const int sprec = ctx->prec == HBE_FP64 ? 0 : 1;
   const bool kahan = is_kahan(ctx->prec);
   const size_t plane = (size_t)N * N;
-  if (device) {
-    CK(launch_pack(sprec, phi0, ctx->f[F_P0], kahan ? ctx->f[F_PLO0] : nullptr, N, ctx->pitch_s,
+  const double *dp0 = device ? phi0 : static_cast<const double *>(pinned_device_ptr(phi0));
+  const double *dp1 = device ? phi1 : static_cast<const double *>(pinned_device_ptr(phi1));
+  if (dp0 && dp1) {
+    // device arrays, or page-locked host arrays read by the pack kernel itself
+    CK(launch_pack(sprec, dp0, ctx->f[F_P0], kahan ? ctx->f[F_PLO0] : nullptr, N, ctx->pitch_s,
                    ctx->hxs, ctx->bc, 0, N, ctx->stream));
-    CK(launch_pack(sprec, phi1, ctx->f[F_Q0], kahan ? ctx->f[F_QLO0] : nullptr, N, ctx->pitch_s,
+    CK(launch_pack(sprec, dp1, ctx->f[F_Q0], kahan ? ctx->f[F_QLO0] : nullptr, N, ctx->pitch_s,
                    ctx->hxs, ctx->bc, 0, N, ctx->stream));
+    if (!device) CK(cudaStreamSynchronize(ctx->stream));
   } else {
     // chunks of planes through two staging sets: the copy of chunk i + 1
     // (copy stream) overlaps the pack of chunk i (work stream)
@@ -947,9 +965,13 @@ static hbe_status read_impl(hbe_ctx *ctx, double *phi, double *psi, bool device)
   const int set = (int)(ctx->h_desc->n_base & 1);
   void *hp = ctx->f[F_P0 + set], *hq = ctx->f[F_Q0 + set];
   void *lp = kahan ? ctx->f[F_PLO0 + set] : nullptr, *lq = kahan ? ctx->f[F_QLO0 + set] : nullptr;
-  if (device) {
-    if (phi) CK(launch_unpack(sprec, hp, lp, phi, N, ctx->pitch_s, ctx->hxs, 0, N, ctx->stream));
-    if (psi) CK(launch_unpack(sprec, hq, lq, psi, N, ctx->pitch_s, ctx->hxs, 0, N, ctx->stream));
+  double *dphi = device || !phi ? phi : static_cast<double *>(const_cast<void *>(pinned_device_ptr(phi)));
+  double *dpsi = device || !psi ? psi : static_cast<double *>(const_cast<void *>(pinned_device_ptr(psi)));
+  if ((!phi || dphi) && (!psi || dpsi)) {
+    // device arrays, or page-locked host arrays written by the unpack kernel itself
+    if (phi) CK(launch_unpack(sprec, hp, lp, dphi, N, ctx->pitch_s, ctx->hxs, 0, N, ctx->stream));
+    if (psi) CK(launch_unpack(sprec, hq, lq, dpsi, N, ctx->pitch_s, ctx->hxs, 0, N, ctx->stream));
+    if (!device) CK(cudaStreamSynchronize(ctx->stream));
     return HBE_OK;
   }
   // chunks of planes through two staging sets: the unpack of chunk i + 1
