@@ -320,8 +320,19 @@ hbe_status hbe_batch_add(hbe_batch *b, hbe_ctx *ctx, int64_t nsteps, double dt);
 hbe_status hbe_batch_remove(hbe_batch *b, hbe_ctx *ctx);
 /* One run: up to K steps for every member.  On return *n_finished holds how
  * many members reached their step count or stopped, listed in finished[]
- * (capacity max_finished); they are removed from the batch. */
+ * (capacity max_finished); they are removed from the batch.  Equivalent to
+ * hbe_batch_launch followed by hbe_batch_collect. */
 hbe_status hbe_batch_run(hbe_batch *b, hbe_ctx **finished, int max_finished, int *n_finished);
+/* The two halves of hbe_batch_run.  hbe_batch_launch enqueues one run on the
+ * batch's stream and returns at once; hbe_batch_collect waits for it and
+ * retires the members that finished, as hbe_batch_run does.  Between the two
+ * the host may work on members retired earlier (read them, run diagnostics
+ * on another stream); hbe_batch_add, hbe_batch_remove and a second launch
+ * return HBE_ESTATE until the run is collected.  Collecting with no run in
+ * flight returns HBE_OK and no members. */
+hbe_status hbe_batch_launch(hbe_batch *b);
+hbe_status hbe_batch_collect(hbe_batch *b, hbe_ctx **finished, int max_finished,
+                             int *n_finished);
 int hbe_batch_size(const hbe_batch *b);
 const char *hbe_batch_last_error(const hbe_batch *b);
 int64_t hbe_batch_launch_count(const hbe_batch *b);

@@ -22,7 +22,8 @@ EXPORTS = (
     "hbe_set_initial_device", "hbe_set_initial_bumps", "hbe_set_stop", "hbe_step", "hbe_step_async", "hbe_sync",
     "hbe_read", "hbe_read_device", "hbe_profile_stages", "hbe_progress", "hbe_analysis", "hbe_diag", "hbe_save", "hbe_load",
     "hbe_last_error", "hbe_status_string", "hbe_launch_count", "hbe_batch_create",
-    "hbe_batch_destroy", "hbe_batch_add", "hbe_batch_remove", "hbe_batch_run",
+    "hbe_batch_destroy", "hbe_batch_add", "hbe_batch_remove", "hbe_batch_run", "hbe_batch_launch",
+    "hbe_batch_collect",
     "hbe_batch_size", "hbe_batch_last_error", "hbe_batch_launch_count", "hbe_step_fp64_noalloc",
     "hbe_radial_max_n", "hbe_radial_run",
 )
@@ -111,6 +112,8 @@ def load() -> ctypes.CDLL:
             "hbe_batch_add": (I, [P, P, I64, D]),
             "hbe_batch_remove": (I, [P, P]),
             "hbe_batch_run": (I, [P, ctypes.POINTER(P), I, ctypes.POINTER(I)]),
+            "hbe_batch_launch": (I, [P]),
+            "hbe_batch_collect": (I, [P, ctypes.POINTER(P), I, ctypes.POINTER(I)]),
             "hbe_batch_size": (I, [P]),
             "hbe_batch_last_error": (ctypes.c_char_p, [P]),
             "hbe_batch_launch_count": (I64, [P]),

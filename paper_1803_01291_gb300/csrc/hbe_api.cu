@@ -81,7 +81,9 @@ struct hbe_ctx {
   int schedule = 1;  // 0: four one-stage kernels per step; 1: two fused stage pairs
   unsigned *d_err = nullptr;
   int K = 8;
-  cudaGraphExec_t gexec = nullptr;
+  // gexec[n]: graph of n RK4 steps (n = K for the full replays, n < K for the
+  // last replay of a call whose step count is not a multiple of K)
+  cudaGraphExec_t gexec[kMaxK + 1] = {};
   double *d_stage = nullptr;   // 2 buffer sets x 2 fields x stage_elems doubles
   size_t stage_elems = 0;
   cudaStream_t copy_stream = nullptr;   // host <-> staging copies
@@ -113,9 +115,14 @@ struct hbe_batch {
   } lists[kMaxVariants], lists_p[kMaxVariants];  // lists_p: the stages 1+2 kernel's tiles
   int nvariants = 0;
   unsigned *d_err = nullptr;
+  unsigned *h_err = nullptr;    // pinned copy of d_err, read after a run
   cudaGraphExec_t gexec = nullptr;
+  unsigned graph_variants = 0;  // bit v: the captured graph launches variant v's kernels
   bool dirty = true;
   bool wraps = false;  // the captured graph has the periodic ghost copies
+  bool in_flight = false;       // a run is enqueued and not yet collected
+  int run_members = 0;          // members of the run in flight
+  cudaEvent_t ev_done = nullptr;
   int64_t launches = 0;
   std::string err;
 };
@@ -220,6 +227,14 @@ void build_items(const hbe_ctx *ctx, int member, int zchunk, int kidx, std::vect
         out.push_back(make_int4(member, i | (j << 16), z0, std::min(zchunk, ctx->N - z0)));
 }
 
+void drop_graphs(hbe_ctx *ctx) {
+  for (auto &g : ctx->gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
 hbe_status apply_tuning(hbe_ctx *ctx, int variant, int zchunk) {
   const VariantTable &vt = table_for(ctx->prec);
   if (variant < 0 || variant >= vt.count)
@@ -289,10 +304,7 @@ hbe_status apply_tuning(hbe_ctx *ctx, int variant, int zchunk) {
   }
   for (int s = 0; s < 6; ++s)
     ctx->grid[s] = std::min(ctx->grid[s], s == 4 ? ctx->nitems_p : ctx->nitems);
-  if (ctx->gexec) {
-    cudaGraphExecDestroy(ctx->gexec);
-    ctx->gexec = nullptr;
-  }
+  drop_graphs(ctx);
   return HBE_OK;
 }
 
@@ -355,16 +367,18 @@ int launches_per_step(const hbe_ctx *ctx) {
   return n;
 }
 
-hbe_status ensure_graph(hbe_ctx *ctx) {
-  if (ctx->gexec) return HBE_OK;
+// The graph of nk RK4 steps: step coefficients, nk x (stage kernels + ghost
+// copies), advance.
+hbe_status ensure_graph(hbe_ctx *ctx, int nk) {
+  if (ctx->gexec[nk]) return HBE_OK;
   const VariantTable &vt = table_for(ctx->prec);
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
   hbe_status st = HBE_OK;
   const int first = ctx->schedule ? 4 : 0, last = ctx->schedule ? 6 : 4;
-  cudaError_t ec = launch_coef(ctx->d_desc, ctx->d_one, 1, ctx->K, ctx->cap_stream);
+  cudaError_t ec = launch_coef(ctx->d_desc, ctx->d_one, 1, nk, ctx->cap_stream);
   if (ec != cudaSuccess) st = set_err(ctx->err, HBE_ECUDA, "%s", cudaGetErrorString(ec));
-  for (int k = 0; k < ctx->K && st == HBE_OK; ++k)
+  for (int k = 0; k < nk && st == HBE_OK; ++k)
     for (int s = first; s < last && st == HBE_OK; ++s) {
       st = launch_stage(ctx->err, vt.k[ctx->variant][s], ctx->grid[s], ctx_params(ctx, s, k),
                         ctx->cap_stream);
@@ -374,12 +388,12 @@ hbe_status ensure_graph(hbe_ctx *ctx) {
         if (ew != cudaSuccess) st = set_err(ctx->err, HBE_ECUDA, "%s", cudaGetErrorString(ew));
       }
     }
-  cudaError_t e = launch_advance(ctx->d_desc, ctx->d_one, 1, ctx->K, ctx->cap_stream);
+  cudaError_t e = launch_advance(ctx->d_desc, ctx->d_one, 1, nk, ctx->cap_stream);
   cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
   if (st != HBE_OK) return st;
   CK(e);
   CK(e2);
-  e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+  e = cudaGraphInstantiate(&ctx->gexec[nk], g, 0);
   cudaGraphDestroy(g);
   CK(e);
   return HBE_OK;
@@ -603,7 +617,7 @@ hbe_status hbe_create_in(int N, double L, double mu, double lambda, int bc, int 
 void hbe_destroy(hbe_ctx *ctx) {
   if (!ctx) return;
   if (ctx->stream || ctx->cap_stream) cudaStreamSynchronize(ctx->stream);
-  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  drop_graphs(ctx);
   if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
   cudaFree(ctx->d_tmaps);
   cudaFree(ctx->d_maxabs);
@@ -677,10 +691,7 @@ hbe_status hbe_set_schedule(hbe_ctx *ctx, int schedule) {
     hbe_status st = sync_ctx(ctx);
     if (st != HBE_OK) return st;
   }
-  if (ctx->schedule != schedule && ctx->gexec) {
-    cudaGraphExecDestroy(ctx->gexec);
-    ctx->gexec = nullptr;
-  }
+  if (ctx->schedule != schedule) drop_graphs(ctx);
   ctx->schedule = schedule;
   return HBE_OK;
 }
@@ -848,7 +859,12 @@ hbe_status hbe_step_async(hbe_ctx *ctx, int64_t nsteps, double dt) {
   if (ctx->desc_stale) {
     if ((st = push_desc(ctx)) != HBE_OK) return st;
   }
-  if ((st = ensure_graph(ctx)) != HBE_OK) return st;
+  // whole replays of K steps, then one replay of the remaining steps (its own
+  // graph), so no replay launches kernels for steps that are not taken
+  const int64_t full = nsteps / ctx->K;
+  const int rem = (int)(nsteps % ctx->K);
+  if (full > 0 && (st = ensure_graph(ctx, ctx->K)) != HBE_OK) return st;
+  if (rem > 0 && (st = ensure_graph(ctx, rem)) != HBE_OK) return st;
   if (!ctx->pending) {
     // restart: clear the stop status; a new dt moves the time origin to the current t
     if (dt != d.dt) {
@@ -860,9 +876,9 @@ hbe_status hbe_step_async(hbe_ctx *ctx, int64_t nsteps, double dt) {
   } else {
     CK(launch_set_run(ctx->d_desc, nsteps, d.t0, d.dt, d.stop_thr, 0, ctx->stream));
   }
-  const int64_t runs = (nsteps + ctx->K - 1) / ctx->K;
-  for (int64_t r = 0; r < runs; ++r) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
-  ctx->launches += runs * launches_per_step(ctx) * ctx->K;
+  for (int64_t r = 0; r < full; ++r) CK(cudaGraphLaunch(ctx->gexec[ctx->K], ctx->stream));
+  if (rem > 0) CK(cudaGraphLaunch(ctx->gexec[rem], ctx->stream));
+  ctx->launches += nsteps * launches_per_step(ctx);
   ctx->pending = true;
   return HBE_OK;
 }
@@ -1196,7 +1212,9 @@ hbe_status hbe_batch_create(int prec, int K, void *stream, hbe_batch **out) {
       cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMalloc(&b->d_err, sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(b->d_err, 0, sizeof(unsigned)) != cudaSuccess ||
-      cudaMalloc(&b->d_ndesc, sizeof(int)) != cudaSuccess) {
+      cudaMalloc(&b->d_ndesc, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&b->h_err, sizeof(unsigned)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming) != cudaSuccess) {
     hbe_batch_destroy(b);
     return HBE_ECUDA;
   }
@@ -1218,6 +1236,8 @@ void hbe_batch_destroy(hbe_batch *b) {
       cudaFree(ls[v].d_n);
     }
   cudaFree(b->d_err);
+  if (b->h_err) cudaFreeHost(b->h_err);
+  if (b->ev_done) cudaEventDestroy(b->ev_done);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   delete b;
 }
@@ -1228,6 +1248,7 @@ int64_t hbe_batch_launch_count(const hbe_batch *b) { return b ? b->launches : 0;
 
 hbe_status hbe_batch_add(hbe_batch *b, hbe_ctx *ctx, int64_t nsteps, double dt) {
   if (!b || !ctx) return HBE_EINVAL;
+  if (b->in_flight) return set_err(b->err, HBE_ESTATE, "a run is in flight: collect it first");
   if (ctx->prec != b->prec) return set_err(b->err, HBE_EINVAL, "precision differs from the batch");
   if (ctx->in_batch) return set_err(b->err, HBE_ESTATE, "context already in a batch");
   if (!ctx->has_state) return set_err(b->err, HBE_ESTATE, "context has no initial data");
@@ -1256,6 +1277,7 @@ static void leave_batch(hbe_ctx *ctx) {
 
 hbe_status hbe_batch_remove(hbe_batch *b, hbe_ctx *ctx) {
   if (!b || !ctx) return HBE_EINVAL;
+  if (b->in_flight) return set_err(b->err, HBE_ESTATE, "a run is in flight: collect it first");
   auto it = std::find(b->members.begin(), b->members.end(), ctx);
   if (it == b->members.end()) return set_err(b->err, HBE_EINVAL, "not a member");
   cudaStreamSynchronize(b->stream);
@@ -1269,8 +1291,15 @@ static hbe_status batch_rebuild(hbe_batch *b) {
   const int M = (int)b->members.size();
   bool recapture = !b->gexec;
   bool periodic = false;
-  for (hbe_ctx *c : b->members) periodic |= c->bc == HBE_BC_PERIODIC;
+  unsigned used = 0;
+  for (hbe_ctx *c : b->members) {
+    periodic |= c->bc == HBE_BC_PERIODIC;
+    used |= 1u << c->variant;
+  }
   if (periodic && !b->wraps) recapture = true;
+  // the graph launches the kernels of the variants that have members (kept
+  // while members of other variants come and go, so joins rarely re-capture)
+  if ((used & ~b->graph_variants) != 0) recapture = true;
   if (M > b->cap_desc) {
     int cap = std::max(64, b->cap_desc);
     while (cap < M) cap *= 2;
@@ -1328,11 +1357,12 @@ static hbe_status batch_rebuild(hbe_batch *b) {
     cudaError_t ec = launch_coef(b->d_descs, b->d_ndesc, b->cap_desc, b->K, b->cap_stream);
     if (ec != cudaSuccess) st = set_err(b->err, HBE_ECUDA, "%s", cudaGetErrorString(ec));
     // the batch always runs the fused stage pairs (kernels 4 and 5 of a variant)
+    const unsigned gv = used;
     for (int k = 0; k < b->K && st == HBE_OK; ++k)
       for (int s = 4; s < 6 && st == HBE_OK; ++s) {
         for (int v = 0; v < b->nvariants && st == HBE_OK; ++v) {
           auto &l = s == 4 ? b->lists_p[v] : b->lists[v];
-          if (!l.d_n) continue;
+          if (!l.d_n || !(gv >> v & 1u)) continue;
           StageParams p{b->d_descs, l.d_items, l.d_n, b->d_err, k};
           st = launch_stage(b->err, vt.k[v][s], l.grid[s], p, b->cap_stream);
         }
@@ -1344,6 +1374,7 @@ static hbe_status batch_rebuild(hbe_batch *b) {
         }
       }
     b->wraps = periodic;
+    b->graph_variants = gv;
     cudaError_t e = launch_advance(b->d_descs, b->d_ndesc, b->cap_desc, b->K, b->cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
     if (st != HBE_OK) return st;
@@ -1357,10 +1388,10 @@ static hbe_status batch_rebuild(hbe_batch *b) {
   return HBE_OK;
 }
 
-hbe_status hbe_batch_run(hbe_batch *b, hbe_ctx **finished, int max_finished, int *n_finished) {
-  Range range_("hbe_batch_run");
-  if (!b || !n_finished) return HBE_EINVAL;
-  *n_finished = 0;
+hbe_status hbe_batch_launch(hbe_batch *b) {
+  Range range_("hbe_batch_launch");
+  if (!b) return HBE_EINVAL;
+  if (b->in_flight) return set_err(b->err, HBE_ESTATE, "a run is in flight: collect it first");
   if (b->members.empty()) return HBE_OK;
   if (b->dirty) {
     hbe_status st = batch_rebuild(b);
@@ -1369,14 +1400,29 @@ hbe_status hbe_batch_run(hbe_batch *b, hbe_ctx **finished, int max_finished, int
   const int M = (int)b->members.size();
   CKX(b->err, cudaGraphLaunch(b->gexec, b->stream));
   int used = 0;
-  for (int v = 0; v < b->nvariants; ++v) used += b->lists[v].d_n ? 1 : 0;
+  for (int v = 0; v < b->nvariants; ++v) used += (b->graph_variants >> v & 1u) ? 1 : 0;
   b->launches += (int64_t)(2 * used + (b->wraps ? 2 : 0)) * b->K;
+  // the members' descriptors and the error word come back behind the run
   CKX(b->err, cudaMemcpyAsync(b->h_descs, b->d_descs, M * sizeof(Desc), cudaMemcpyDeviceToHost,
                               b->stream));
-  CKX(b->err, cudaStreamSynchronize(b->stream));
-  unsigned e = 0;
-  CKX(b->err, cudaMemcpy(&e, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
-  if (e) return set_err(b->err, HBE_ETIMEOUT, "a stage kernel's TMA wait timed out");
+  CKX(b->err, cudaMemcpyAsync(b->h_err, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                              b->stream));
+  CKX(b->err, cudaEventRecord(b->ev_done, b->stream));
+  b->in_flight = true;
+  b->run_members = M;
+  return HBE_OK;
+}
+
+hbe_status hbe_batch_collect(hbe_batch *b, hbe_ctx **finished, int max_finished,
+                             int *n_finished) {
+  Range range_("hbe_batch_collect");
+  if (!b || !n_finished) return HBE_EINVAL;
+  *n_finished = 0;
+  if (!b->in_flight) return HBE_OK;
+  b->in_flight = false;
+  CKX(b->err, cudaEventSynchronize(b->ev_done));
+  if (*b->h_err) return set_err(b->err, HBE_ETIMEOUT, "a stage kernel's TMA wait timed out");
+  const int M = b->run_members;
   std::vector<hbe_ctx *> keep;
   for (int i = 0; i < M; ++i) {
     hbe_ctx *c = b->members[i];
@@ -1394,6 +1440,15 @@ hbe_status hbe_batch_run(hbe_batch *b, hbe_ctx **finished, int max_finished, int
   }
   b->members.swap(keep);
   return HBE_OK;
+}
+
+hbe_status hbe_batch_run(hbe_batch *b, hbe_ctx **finished, int max_finished, int *n_finished) {
+  Range range_("hbe_batch_run");
+  if (!b || !n_finished) return HBE_EINVAL;
+  *n_finished = 0;
+  hbe_status st = hbe_batch_launch(b);
+  if (st != HBE_OK) return st;
+  return hbe_batch_collect(b, finished, max_finished, n_finished);
 }
 
 }  // extern "C"

@@ -8,7 +8,9 @@ which each stage is a single persistent kernel launch over the tiles of all
 members (libhbe's batched runner).  Members leave the batch the moment they
 reach their step count (or the stop rule fires), their result is read back,
 their memory is released and waiting requests take their place — new work
-joins between graph replays without re-capturing the graph.
+joins between graph replays without re-capturing the graph.  The next run
+is enqueued before the finished members are retired, and their diagnostics
+run on a second stream, so the GPU does not wait for the host between runs.
 
 Each member's arithmetic per grid point is the same as when it runs alone,
 so results do not depend on what else is in the batch (bitwise).
@@ -118,6 +120,7 @@ class Server:
         self._small_variant = None
         self.in_use = 0
         self._live: Dict[int, tuple] = {}
+        self._side = None  # stream of the retirement work (diagnostics, reads)
 
     def need_bytes(self, req: SolveRequest) -> int:
         return workspace_bytes(req.N, req.bc, self.prec)
@@ -171,7 +174,13 @@ class Server:
         stats = ServeStats()
         t0 = clock()
         i = 0
-        while i < len(pending) or len(self.batch):
+        in_flight = False
+        while i < len(pending) or len(self.batch) or in_flight:
+            # the run in flight: wait for it, take its finished members out
+            done = []
+            if in_flight:
+                done = self.batch.collect()
+                in_flight = False
             now = clock() - t0
             # admission: arrived, fits in memory, slot free (FIFO, no overtaking)
             while i < len(pending):
@@ -192,30 +201,45 @@ class Server:
                 i += 1
             stats.peak_members = max(stats.peak_members, len(self.batch))
             stats.peak_bytes = max(stats.peak_bytes, self.in_use)
-            if not len(self.batch):
-                if i < len(pending):
-                    wait = pending[i].arrival - (clock() - t0)
-                    if wait > 0:
-                        time.sleep(min(wait, 0.05))
-                continue
-            l0 = self.batch.launches
-            done = self.batch.run()
-            stats.launches += self.batch.launches - l0
-            stats.runs += 1
-            for s in done:
-                req, _, admitted, nb = self._live.pop(s.handle.value)
-                st = s.sync()
-                steps, _ = s.progress()
-                d = s.diag()  # the result: max|phi|, finiteness, bubble count
-                phi = s.read(psi=False)[0] if self.keep_fields else None
-                # closed-loop runs treat every request as arrived at the start
-                arrived = req.arrival if realtime else 0.0
-                stats.results.append(Result(req.rid, arrived, admitted, clock() - t0, steps,
-                                            st, d["max_abs_phi"], phi))
-                s.close()
-                self.in_use -= nb
+            # the next run goes to the GPU before the finished members are
+            # retired, so their diagnostics and reads overlap it
+            if len(self.batch):
+                l0 = self.batch.launches
+                self.batch.launch()
+                in_flight = True
+                stats.launches += self.batch.launches - l0
+                stats.runs += 1
+            self._retire(done, stats, t0, clock, realtime)
+            if not in_flight and not done and i < len(pending):
+                wait = pending[i].arrival - (clock() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.05))
         stats.makespan = clock() - t0
         return stats
+
+    def _retire(self, done, stats: ServeStats, t0: float, clock, realtime: bool):
+        """Results of the members that left the batch: status, step count, the
+        diagnostics (max|phi|, bubble count) and optionally phi, computed on a
+        side stream while the batch's next run occupies the main one."""
+        if not done:
+            return
+        torch = self.torch
+        if self._side is None and torch.cuda.is_available():
+            self._side = torch.cuda.Stream()
+        for s in done:
+            req, _, admitted, nb = self._live.pop(s.handle.value)
+            st = s.sync()
+            steps, _ = s.progress()
+            if self._side is not None:
+                s.set_stream(self._side.cuda_stream)
+            d = s.diag()  # the result: max|phi|, finiteness, bubble count
+            phi = s.read(psi=False)[0] if self.keep_fields else None
+            # closed-loop runs treat every request as arrived at the start
+            arrived = req.arrival if realtime else 0.0
+            stats.results.append(Result(req.rid, arrived, admitted, clock() - t0, steps,
+                                        st, d["max_abs_phi"], phi))
+            s.close()
+            self.in_use -= nb
 
     def close(self):
         self.batch.close()

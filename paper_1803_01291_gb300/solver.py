@@ -112,6 +112,10 @@ class Solver:
         return self.L / self.N if self.bc == PERIODIC else self.L / (self.N + 1)
 
     # -- API
+    def set_stream(self, stream: int):
+        """Enqueue this problem's later work on `stream` (a cudaStream_t)."""
+        self._chk(self.lib.hbe_set_stream(self._ctx, ctypes.c_void_p(int(stream))))
+
     def set_tuning(self, variant: int, zchunk: int = 0):
         self._chk(self.lib.hbe_set_tuning(self._ctx, variant, zchunk))
 
@@ -262,10 +266,21 @@ class Batch:
         self._members.pop(solver.handle.value, None)
 
     def run(self) -> List[Solver]:
+        """One run of up to K steps for every member; returns the members that
+        finished (reached their step count or stopped)."""
+        self.launch()
+        return self.collect()
+
+    def launch(self):
+        """Enqueue one run and return at once (collect() waits for it)."""
+        self._chk(self.lib.hbe_batch_launch(self._b))
+
+    def collect(self) -> List[Solver]:
+        """Wait for the run in flight and return the members that finished."""
         cap = max(1, len(self._members))
         arr = (ctypes.c_void_p * cap)()
         n = ctypes.c_int()
-        self._chk(self.lib.hbe_batch_run(self._b, arr, cap, ctypes.byref(n)))
+        self._chk(self.lib.hbe_batch_collect(self._b, arr, cap, ctypes.byref(n)))
         done = [self._members.pop(arr[i]) for i in range(n.value)]
         return done
 

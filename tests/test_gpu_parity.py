@@ -204,6 +204,27 @@ def test_split_steps_equal_one_call(hbe):
         assert np.array_equal(a, b) and np.array_equal(aq, bq)
 
 
+def test_partial_replays_launch_only_taken_steps(hbe):
+    """A call whose step count is not a multiple of the graph length K = 8
+    ends with a graph of the remaining steps: 11 steps launch 11 steps' worth
+    of kernels (2 stage pairs + 2 periodic ghost copies each), and 11 calls of
+    one step (11 one-step graphs) give the same bits as one call of 11."""
+    prob = rand_problem(28, 1, seed=21)
+    for prec in (0, 1):
+        with hbe.Solver(prob.N, prob.L, prob.mu, prob.lam, 1, prec) as s:
+            s.set_initial(prob.phi0, prob.phi1)
+            l0 = s.launches
+            s.step(11, prob.dt)
+            assert s.launches - l0 == 11 * 4
+            a, aq, _ = s.read()
+        with hbe.Solver(prob.N, prob.L, prob.mu, prob.lam, 1, prec) as s:
+            s.set_initial(prob.phi0, prob.phi1)
+            for _ in range(11):
+                s.step(1, prob.dt)
+            b, bq, _ = s.read()
+        assert np.array_equal(a, b) and np.array_equal(aq, bq)
+
+
 def test_batch_alone_equals_mixed(hbe):
     """Members of a batch (mixed sizes, parameters, step counts) end bit for
     bit where they end when stepped alone."""

@@ -90,3 +90,50 @@ def test_server_requeues_after_allocation_failure(hbe, monkeypatch):
             s.set_initial_bumps(q.bumps)
             s.step(q.nsteps, q.dt)
             assert s.diag()["max_abs_phi"] == by_id[q.rid].max_abs_phi
+
+
+def test_server_fields_equal_alone_bitwise(hbe):
+    """Every request's final phi, read through the server (keep_fields), is
+    the same bits as the problem solved alone: the batched runner, the
+    pipelined runs and the side-stream retirement change nothing."""
+    from paper_1803_01291_gb300 import serve
+    reqs = serve.requests_from_stream(small_stream(8, 13))
+    srv = serve.Server(hbe.FP32, K=4, keep_fields=True)
+    stats = srv.run(reqs, realtime=False)
+    srv.close()
+    by_id = {r.rid: r for r in stats.results}
+    assert sorted(by_id) == sorted(q.rid for q in reqs)
+    for q in reqs:
+        res = by_id[q.rid]
+        assert res.phi is not None and res.steps == q.nsteps
+        with hbe.Solver(q.N, q.L, q.mu, q.lam, 0, hbe.FP32) as s:
+            s.set_initial_bumps(q.bumps)
+            s.step(q.nsteps, q.dt)
+            alone = s.read(psi=False)[0]
+        assert np.array_equal(res.phi, alone), q.rid
+
+
+def test_batch_launch_collect_protocol(hbe):
+    """launch enqueues, collect retires; membership changes wait for collect."""
+    r = small_stream(2, 17)
+    b = hbe.Batch(hbe.FP32, K=4)
+    ss = []
+    for q in r:
+        s = hbe.Solver(q.N, q.L, q.mu, q.lam, 0, hbe.FP32)
+        s.set_initial_bumps(q.bumps)
+        ss.append(s)
+    b.add(ss[0], 6, 0.01)
+    assert b.collect() == []          # nothing in flight
+    b.launch()
+    with pytest.raises(hbe.HBEError):
+        b.add(ss[1], 6, 0.01)         # a run is in flight
+    with pytest.raises(hbe.HBEError):
+        b.launch()
+    assert b.collect() == []          # 4 of 6 steps done
+    b.add(ss[1], 6, 0.01)
+    done = b.run()
+    assert done == [ss[0]]
+    assert ss[0].progress()[0] == 6
+    b.close()
+    for s in ss:
+        s.close()

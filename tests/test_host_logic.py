@@ -87,6 +87,9 @@ class FakeSolver:
     def sync(self):
         return _lib.OK
 
+    def set_stream(self, stream):
+        pass
+
     def progress(self):
         return self.steps, 0.0
 
@@ -101,20 +104,32 @@ class FakeBatch:
     def __init__(self, prec, K):
         self.K, self.members, self.launches = K, [], 0
         self.max_seen = 0
+        self.in_flight = False
 
     def add(self, s, nsteps, dt):
+        assert not self.in_flight, "add with a run in flight"
         s.target = nsteps
         self.members.append(s)
         self.max_seen = max(self.max_seen, len(self.members))
 
-    def run(self):
-        done = []
+    def launch(self):
+        assert not self.in_flight, "launch with a run in flight"
         for s in self.members:
             s.steps = min(s.target, s.steps + self.K)
         self.launches += 2 * self.K
+        self.in_flight = True
+
+    def collect(self):
+        if not self.in_flight:
+            return []
+        self.in_flight = False
         done = [s for s in self.members if s.steps >= s.target]
         self.members = [s for s in self.members if s.steps < s.target]
         return done
+
+    def run(self):
+        self.launch()
+        return self.collect()
 
     def __len__(self):
         return len(self.members)
