@@ -337,6 +337,42 @@ int hbe_batch_size(const hbe_batch *b);
 const char *hbe_batch_last_error(const hbe_batch *b);
 int64_t hbe_batch_launch_count(const hbe_batch *b);
 
+/* ---- z-slab decomposition (virtual slabs on one GPU) ------------------- */
+/* The grid split along z into k slabs that exchange 2-plane halos after each
+ * fused stage pair, the partitioning a run over several GPUs would use (the
+ * stencil of Sec. 2.1 reaches 2 planes, so every stage argument read with a
+ * halo -- phi, psi after stages 3+4, G1, G2 after stages 1+2 -- needs 2 planes
+ * of each neighbour).  Here all slabs live on the current device and the
+ * halos are plain device copies into the receiving slab's own buffers; the
+ * result is bitwise that of the undivided grid. */
+typedef struct hbe_slabs hbe_slabs;
+
+/* The exchange plan: nz[i] = planes of slab i (N/k, +1 for the first N % k
+ * slabs); each transfer is 4 ints (source slab, destination slab, first
+ * stored plane at the source, first halo plane at the destination), 2
+ * planes each.  A slab stores its nz planes at stored planes 2 .. nz+1, with
+ * halo planes 0, 1 below and nz+2, nz+3 above.  Periodic: slab 0 and slab k-1
+ * are neighbours.  Pure host function (no CUDA call).  Returns the number of
+ * transfers (2k periodic, 2k - 2 Dirichlet; copies may be NULL to count), or
+ * -1 if k < 1, N < 2k or max_copies is too small. */
+int hbe_slab_plan(int N, int k, int periodic, int32_t *nz, int32_t *copies, int max_copies);
+
+/* k slabs of the problem of hbe_create (same arguments), work on `stream`
+ * (cudaStream_t, NULL = legacy default).  No stop threshold: a slab that
+ * turns non-finite ends the steps of all slabs with HBE_NONFINITE. */
+hbe_status hbe_slabs_create(int N, double L, double mu, double lambda, int bc, int prec, int k,
+                            void *stream, hbe_slabs **out);
+void hbe_slabs_destroy(hbe_slabs *s);
+/* Initial data from device arrays of N^3 doubles (x fastest); blocks. */
+hbe_status hbe_slabs_set_initial_device(hbe_slabs *s, const double *d_phi0,
+                                        const double *d_phi1, double t0);
+/* nsteps RK4 steps of size dt on every slab (blocks until done). */
+hbe_status hbe_slabs_step(hbe_slabs *s, int64_t nsteps, double dt);
+/* The whole grid's state into device arrays of N^3 doubles (either may be
+ * NULL) and the current time. */
+hbe_status hbe_slabs_read_device(hbe_slabs *s, double *d_phi, double *d_psi, double *t);
+const char *hbe_slabs_last_error(const hbe_slabs *s);
+
 #ifdef __cplusplus
 }
 #endif

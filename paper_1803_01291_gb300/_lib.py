@@ -25,7 +25,9 @@ EXPORTS = (
     "hbe_batch_destroy", "hbe_batch_add", "hbe_batch_remove", "hbe_batch_run", "hbe_batch_launch",
     "hbe_batch_collect",
     "hbe_batch_size", "hbe_batch_last_error", "hbe_batch_launch_count", "hbe_step_fp64_noalloc",
-    "hbe_radial_max_n", "hbe_radial_run",
+    "hbe_radial_max_n", "hbe_radial_run", "hbe_slab_plan", "hbe_slabs_create",
+    "hbe_slabs_destroy", "hbe_slabs_set_initial_device", "hbe_slabs_step",
+    "hbe_slabs_read_device", "hbe_slabs_last_error",
 )
 
 
@@ -118,6 +120,14 @@ def load() -> ctypes.CDLL:
             "hbe_batch_last_error": (ctypes.c_char_p, [P]),
             "hbe_batch_launch_count": (I64, [P]),
             "hbe_step_fp64_noalloc": (I, [I, D, D, D, I, P, P, D, D, I64, P, P, P]),
+            "hbe_slab_plan": (I, [I, I, I, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_int32), I]),
+            "hbe_slabs_create": (I, [I, D, D, D, I, I, I, P, ctypes.POINTER(P)]),
+            "hbe_slabs_destroy": (None, [P]),
+            "hbe_slabs_set_initial_device": (I, [P, P, P, D]),
+            "hbe_slabs_step": (I, [P, I64, D]),
+            "hbe_slabs_read_device": (I, [P, P, P, dp]),
+            "hbe_slabs_last_error": (ctypes.c_char_p, [P]),
             "hbe_radial_max_n": (I, [I]),
             "hbe_radial_run": (I, [I, I, D, P, P, P, P, D, D, I64, I, I, D, D, P, P, P, P, P,
                                    P]),

@@ -53,6 +53,7 @@ int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
 struct hbe_ctx {
   int N = 0, bc = 0, prec = 0;
+  int nz = 0, zoff = 0;  // stored z-planes: nz interior after zoff halo planes (a z-slab: 2)
   double L = 0, mu = 0, lambda = 0, h = 0;
   int device = 0, sms = 0;
   cudaStream_t stream = nullptr;      // user stream (work is enqueued here)
@@ -123,6 +124,10 @@ struct hbe_batch {
   bool in_flight = false;       // a run is enqueued and not yet collected
   int run_members = 0;          // members of the run in flight
   cudaEvent_t ev_done = nullptr;
+  // z-slab decomposition: halo transfers between members (member i = slab i)
+  // after each stage pair; empty for an ordinary batch
+  HaloCopy *d_halo = nullptr;
+  int nhalo = 0;
   int64_t launches = 0;
   std::string err;
 };
@@ -183,7 +188,8 @@ hbe_status get_encoder(std::string &err) {
 // 3D map over a padded field: dims (pitch, N + 4, N), box (bx, by, 1).
 hbe_status encode_map(hbe_ctx *ctx, CUtensorMap *m, void *base, int esize, int pitch, int bx,
                       int by) {
-  cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)(ctx->N + 4), (cuuint64_t)ctx->N};
+  cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)(ctx->N + 4),
+                        (cuuint64_t)(ctx->nz + 2 * ctx->zoff)};
   cuuint64_t strides[2] = {(cuuint64_t)pitch * esize, (cuuint64_t)pitch * (ctx->N + 4) * esize};
   cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
   cuuint32_t estr[3] = {1, 1, 1};
@@ -221,10 +227,10 @@ int auto_zchunk(int N, int columns, int resident) {
 void build_items(const hbe_ctx *ctx, int member, int zchunk, int kidx, std::vector<WorkItem> &out) {
   const KernelInfo &ki = table_for(ctx->prec).k[ctx->variant][kidx];
   const int tx = (ctx->N + ki.tx - 1) / ki.tx, ty = (ctx->N + ki.ty - 1) / ki.ty;
-  for (int z0 = 0; z0 < ctx->N; z0 += zchunk)
+  for (int z0 = 0; z0 < ctx->nz; z0 += zchunk)
     for (int j = 0; j < ty; ++j)
       for (int i = 0; i < tx; ++i)
-        out.push_back(make_int4(member, i | (j << 16), z0, std::min(zchunk, ctx->N - z0)));
+        out.push_back(make_int4(member, i | (j << 16), z0, std::min(zchunk, ctx->nz - z0)));
 }
 
 void drop_graphs(hbe_ctx *ctx) {
@@ -283,9 +289,9 @@ hbe_status apply_tuning(hbe_ctx *ctx, int variant, int zchunk) {
   }
   const int columns = ((ctx->N + tx - 1) / tx) * ((ctx->N + ty - 1) / ty);
   const int columns_p = ((ctx->N + txp - 1) / txp) * ((ctx->N + typ - 1) / typ);
-  ctx->zchunk = zchunk > 0 ? std::min(zchunk, ctx->N) : auto_zchunk(ctx->N, columns, resident);
+  ctx->zchunk = zchunk > 0 ? std::min(zchunk, ctx->nz) : auto_zchunk(ctx->nz, columns, resident);
   ctx->zchunk_p =
-      zchunk > 0 ? std::min(zchunk, ctx->N) : auto_zchunk(ctx->N, columns_p, ctx->grid[4]);
+      zchunk > 0 ? std::min(zchunk, ctx->nz) : auto_zchunk(ctx->nz, columns_p, ctx->grid[4]);
   for (int li = 0; li < 2; ++li) {
     std::vector<WorkItem> items;
     build_items(ctx, 0, li ? ctx->zchunk_p : ctx->zchunk, li ? 4 : 0, items);
@@ -450,8 +456,9 @@ hbe_status validate(std::string &err, int N, double L, double mu, double lambda,
   return HBE_OK;
 }
 
-void layout(int N, int prec, int *hxs, int *hxg, int *ps, int *pg, int64_t *pls, int64_t *plg,
-            size_t *bs, size_t *bg) {
+// Padded layout of a field of N x N x planes stored elements.
+void layout(int N, int planes, int prec, int *hxs, int *hxg, int *ps, int *pg, int64_t *pls,
+            int64_t *plg, size_t *bs, size_t *bg) {
   const int es = state_size(prec), eg = g_size(prec);
   *hxs = 16 / es;
   *hxg = 16 / eg;
@@ -459,15 +466,15 @@ void layout(int N, int prec, int *hxs, int *hxg, int *ps, int *pg, int64_t *pls,
   *pg = round_up(N + 2 * *hxg, *hxg);
   *pls = (int64_t)(N + 4) * *ps;
   *plg = (int64_t)(N + 4) * *pg;
-  *bs = (size_t)(((size_t)*pls * N * es + 255) / 256 * 256);
-  *bg = (size_t)(((size_t)*plg * N * eg + 255) / 256 * 256);
+  *bs = (size_t)(((size_t)*pls * planes * es + 255) / 256 * 256);
+  *bg = (size_t)(((size_t)*plg * planes * eg + 255) / 256 * 256);
 }
 
-size_t workspace_bytes(int N, int prec) {
+size_t workspace_bytes(int N, int prec, int planes) {
   int a, b, c, d;
   int64_t e, f;
   size_t bs, bg;
-  layout(N, prec, &a, &b, &c, &d, &e, &f, &bs, &bg);
+  layout(N, planes, prec, &a, &b, &c, &d, &e, &f, &bs, &bg);
   const int nstate = is_kahan(prec) ? 8 : 4;
   return nstate * bs + 3 * bg;
 }
@@ -490,8 +497,10 @@ bool injected_alloc_failure() {
   return ++count == std::atol(cur.c_str() + 6);
 }
 
+// A context of the N^3 problem storing nz z-planes after zoff halo planes
+// (nz = N, zoff = 0: the whole grid; zoff = 2: one z-slab of a decomposition).
 hbe_status create_common(int N, double L, double mu, double lambda, int bc, int prec, void *ws,
-                         size_t bytes, hbe_ctx **out) {
+                         size_t bytes, hbe_ctx **out, int nz = 0, int zoff = 0) {
   if (!out) return HBE_EINVAL;
   *out = nullptr;
   hbe_ctx *ctx = new hbe_ctx();
@@ -504,15 +513,18 @@ hbe_status create_common(int N, double L, double mu, double lambda, int bc, int 
   if (st != HBE_OK) return bail(st);
   if (injected_alloc_failure()) return bail(HBE_ENOMEM);
   ctx->N = N; ctx->L = L; ctx->mu = mu; ctx->lambda = lambda; ctx->bc = bc; ctx->prec = prec;
+  ctx->nz = nz > 0 ? nz : N;
+  ctx->zoff = zoff;
   ctx->h = bc == HBE_BC_PERIODIC ? L / N : L / (N + 1);
   if (cudaGetDevice(&ctx->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
     set_err(ctx->err, HBE_ECUDA, "no CUDA device");
     return bail(HBE_ECUDA);
   }
-  layout(N, prec, &ctx->hxs, &ctx->hxg, &ctx->pitch_s, &ctx->pitch_g, &ctx->plane_s,
+  const int planes = ctx->nz + 2 * ctx->zoff;
+  layout(N, planes, prec, &ctx->hxs, &ctx->hxg, &ctx->pitch_s, &ctx->pitch_g, &ctx->plane_s,
          &ctx->plane_g, &ctx->bytes_s, &ctx->bytes_g);
-  ctx->ws_bytes = workspace_bytes(N, prec);
+  ctx->ws_bytes = workspace_bytes(N, prec, planes);
   if (ws) {
     if (bytes < ctx->ws_bytes || (reinterpret_cast<uintptr_t>(ws) & 255u)) {
       set_err(ctx->err, HBE_EINVAL, "workspace too small (%zu < %zu) or not 256-byte aligned",
@@ -566,6 +578,8 @@ hbe_status create_common(int N, double L, double mu, double lambda, int bc, int 
   Desc &d = *ctx->h_desc;
   memset(&d, 0, sizeof(Desc));
   d.N = N; d.bc = bc; d.prec = prec;
+  d.nz = ctx->nz; d.zoff = ctx->zoff;
+  d.zwrap = (bc == HBE_BC_PERIODIC && ctx->zoff == 0) ? 1 : 0;
   d.pitch_s = ctx->pitch_s; d.pitch_g = ctx->pitch_g;
   d.plane_s = ctx->plane_s; d.plane_g = ctx->plane_g;
   d.inv_h2 = 1.0 / (ctx->h * ctx->h);
@@ -600,7 +614,7 @@ hbe_status hbe_workspace_bytes(int N, int bc, int prec, size_t *bytes) {
   if (!bytes) return HBE_EINVAL;
   hbe_status st = validate(e, N, 1.0, 0.0, 0.0, bc, prec);
   if (st != HBE_OK) return st;
-  *bytes = workspace_bytes(N, prec);
+  *bytes = workspace_bytes(N, prec, N);
   return HBE_OK;
 }
 
@@ -1236,6 +1250,7 @@ void hbe_batch_destroy(hbe_batch *b) {
       cudaFree(ls[v].d_n);
     }
   cudaFree(b->d_err);
+  cudaFree(b->d_halo);
   if (b->h_err) cudaFreeHost(b->h_err);
   if (b->ev_done) cudaEventDestroy(b->ev_done);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -1372,6 +1387,11 @@ static hbe_status batch_rebuild(hbe_batch *b) {
                                        b->cap_stream);
           if (ew != cudaSuccess) st = set_err(b->err, HBE_ECUDA, "%s", cudaGetErrorString(ew));
         }
+        // halo planes of the stage pair's outputs between the slabs
+        if (st == HBE_OK && b->nhalo > 0) {
+          cudaError_t eh = launch_halo(b->d_descs, b->d_halo, b->nhalo, k, s + 1, b->cap_stream);
+          if (eh != cudaSuccess) st = set_err(b->err, HBE_ECUDA, "%s", cudaGetErrorString(eh));
+        }
       }
     b->wraps = periodic;
     b->graph_variants = gv;
@@ -1401,7 +1421,7 @@ hbe_status hbe_batch_launch(hbe_batch *b) {
   CKX(b->err, cudaGraphLaunch(b->gexec, b->stream));
   int used = 0;
   for (int v = 0; v < b->nvariants; ++v) used += (b->graph_variants >> v & 1u) ? 1 : 0;
-  b->launches += (int64_t)(2 * used + (b->wraps ? 2 : 0)) * b->K;
+  b->launches += (int64_t)(2 * used + (b->wraps ? 2 : 0) + (b->nhalo > 0 ? 2 : 0)) * b->K;
   // the members' descriptors and the error word come back behind the run
   CKX(b->err, cudaMemcpyAsync(b->h_descs, b->d_descs, M * sizeof(Desc), cudaMemcpyDeviceToHost,
                               b->stream));
@@ -1449,6 +1469,198 @@ hbe_status hbe_batch_run(hbe_batch *b, hbe_ctx **finished, int max_finished, int
   hbe_status st = hbe_batch_launch(b);
   if (st != HBE_OK) return st;
   return hbe_batch_collect(b, finished, max_finished, n_finished);
+}
+
+// =============================================================== z-slabs
+// The grid split along z into k slabs of nz_i = N/k (+1 for the first N % k)
+// planes.  Slab i stores its planes after 2 halo planes and before 2 more;
+// after every stage pair the 2 planes next to each slab boundary go into the
+// neighbour's halo planes (the upper neighbour of the last slab and the lower
+// neighbour of the first are each other when periodic; zero-Dirichlet outer
+// halos stay 0, like the out-of-grid planes of an undivided grid).
+int hbe_slab_plan(int N, int k, int periodic, int32_t *nz, int32_t *copies, int max_copies) {
+  if (k < 1 || N < 2 * k || !nz || (periodic != 0 && periodic != 1)) return -1;
+  for (int i = 0; i < k; ++i) nz[i] = N / k + (i < N % k ? 1 : 0);
+  int n = 0;
+  auto add = [&](int src, int dst, int sp, int dp) {
+    if (copies && n < max_copies) {
+      copies[4 * n] = src; copies[4 * n + 1] = dst;
+      copies[4 * n + 2] = sp; copies[4 * n + 3] = dp;
+    }
+    ++n;
+  };
+  for (int i = 0; i < k; ++i) {
+    const int up = i + 1 < k ? i + 1 : (periodic ? 0 : -1);
+    const int down = i > 0 ? i - 1 : (periodic ? k - 1 : -1);
+    // top two interior planes (stored at nz_i, nz_i + 1) -> the upper neighbour's lower halo
+    if (up >= 0) add(i, up, nz[i], 0);
+    // bottom two interior planes (stored at 2, 3) -> the lower neighbour's upper halo
+    if (down >= 0) add(i, down, 2, nz[down] + 2);
+  }
+  return copies && n > max_copies ? -1 : n;
+}
+
+}  // extern "C"
+
+struct hbe_slabs {
+  int N = 0, k = 0, bc = 0, prec = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<hbe_ctx *> parts;
+  std::vector<int> nz, z0;  // planes and first global plane of each slab
+  std::vector<HaloCopy> plan;
+  hbe_batch *batch = nullptr;
+  std::string err;
+};
+
+extern "C" {
+
+void hbe_slabs_destroy(hbe_slabs *s) {
+  if (!s) return;
+  if (s->batch) hbe_batch_destroy(s->batch);
+  for (hbe_ctx *c : s->parts) hbe_destroy(c);
+  delete s;
+}
+
+hbe_status hbe_slabs_create(int N, double L, double mu, double lambda, int bc, int prec, int k,
+                            void *stream, hbe_slabs **out) {
+  if (!out) return HBE_EINVAL;
+  *out = nullptr;
+  hbe_slabs *s = new hbe_slabs();
+  s->N = N; s->k = k; s->bc = bc; s->prec = prec;
+  s->stream = static_cast<cudaStream_t>(stream);
+  std::string e;
+  hbe_status st = validate(e, N, L, mu, lambda, bc, prec);
+  if (st != HBE_OK) { hbe_slabs_destroy(s); return st; }
+  s->nz.assign(k > 0 ? k : 1, 0);
+  const int nc = hbe_slab_plan(N, k, bc == HBE_BC_PERIODIC, s->nz.data(), nullptr, 0);
+  if (nc < 0) { hbe_slabs_destroy(s); return HBE_EINVAL; }
+  std::vector<int32_t> cp(4 * (size_t)std::max(nc, 1));
+  hbe_slab_plan(N, k, bc == HBE_BC_PERIODIC, s->nz.data(), cp.data(), nc);
+  for (int c = 0; c < nc; ++c)
+    s->plan.push_back(HaloCopy{cp[4 * c], cp[4 * c + 1], cp[4 * c + 2], cp[4 * c + 3]});
+  int g = 0;
+  for (int i = 0; i < k; ++i) {
+    s->z0.push_back(g);
+    g += s->nz[i];
+    hbe_ctx *c = nullptr;
+    st = create_common(N, L, mu, lambda, bc, prec, nullptr, 0, &c, s->nz[i], 2);
+    if (st != HBE_OK) { hbe_slabs_destroy(s); return st; }
+    c->stream = s->stream;
+    s->parts.push_back(c);
+  }
+  st = hbe_batch_create(prec, 8, stream, &s->batch);
+  if (st != HBE_OK) { hbe_slabs_destroy(s); return st; }
+  if (nc > 0) {
+    if (cudaMalloc(&s->batch->d_halo, nc * sizeof(HaloCopy)) != cudaSuccess ||
+        cudaMemcpy(s->batch->d_halo, s->plan.data(), nc * sizeof(HaloCopy),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+      hbe_slabs_destroy(s);
+      return HBE_ENOMEM;
+    }
+    s->batch->nhalo = nc;
+  }
+  *out = s;
+  return HBE_OK;
+}
+
+const char *hbe_slabs_last_error(const hbe_slabs *s) { return s ? s->err.c_str() : "null slabs"; }
+
+hbe_status hbe_slabs_set_initial_device(hbe_slabs *s, const double *d_phi0, const double *d_phi1,
+                                        double t0) {
+  Range range_("hbe_slabs_set_initial");
+  if (!s || !d_phi0 || !d_phi1) return HBE_EINVAL;
+  if (!std::isfinite(t0)) return set_err(s->err, HBE_EINVAL, "t0 must be finite");
+  const size_t plane = (size_t)s->N * s->N;
+  for (int i = 0; i < s->k; ++i) {
+    hbe_ctx *c = s->parts[i];
+    hbe_status st = sync_ctx(c);
+    if (st != HBE_OK) return set_err(s->err, st, "%s", c->err.c_str());
+    const int sprec = c->prec == HBE_FP64 ? 0 : 1;
+    const bool kahan = is_kahan(c->prec);
+    // the slab's planes of the global fields into its interior planes
+    CKX(s->err, launch_pack(sprec, d_phi0 + s->z0[i] * plane, c->f[F_P0],
+                            kahan ? c->f[F_PLO0] : nullptr, s->N, c->pitch_s, c->hxs, c->bc,
+                            c->zoff, s->nz[i], s->stream));
+    CKX(s->err, launch_pack(sprec, d_phi1 + s->z0[i] * plane, c->f[F_Q0],
+                            kahan ? c->f[F_QLO0] : nullptr, s->N, c->pitch_s, c->hxs, c->bc,
+                            c->zoff, s->nz[i], s->stream));
+  }
+  // initial halo planes of phi and psi (set 0), plain copies between the slabs
+  for (const HaloCopy &h : s->plan) {
+    hbe_ctx *a = s->parts[h.src], *b = s->parts[h.dst];
+    const size_t pb = (size_t)a->plane_s * state_size(a->prec);
+    for (int f : {F_P0, F_Q0})
+      CKX(s->err, cudaMemcpyAsync(static_cast<char *>(b->f[f]) + h.dst_plane * pb,
+                                  static_cast<const char *>(a->f[f]) + h.src_plane * pb, 2 * pb,
+                                  cudaMemcpyDeviceToDevice, s->stream));
+  }
+  CKX(s->err, cudaStreamSynchronize(s->stream));
+  for (hbe_ctx *c : s->parts) {
+    Desc &d = *c->h_desc;
+    d.t0 = t0; d.dt = 0.0; d.n_base = 0; d.n_end = 0; d.stop_k = kNoStop;
+    d.status = ST_RUNNING; d.last_done = 0;
+    hbe_status st = push_desc(c);
+    if (st != HBE_OK) return set_err(s->err, st, "%s", c->err.c_str());
+    CKX(s->err, cudaMemset(c->d_err, 0, sizeof(unsigned)));
+    c->has_state = true;
+  }
+  return HBE_OK;
+}
+
+hbe_status hbe_slabs_step(hbe_slabs *s, int64_t nsteps, double dt) {
+  Range range_("hbe_slabs_step");
+  if (!s) return HBE_EINVAL;
+  if (nsteps < 0) return set_err(s->err, HBE_EINVAL, "nsteps < 0");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return set_err(s->err, HBE_EINVAL, "dt must be > 0");
+  if (nsteps == 0) return HBE_OK;
+  for (hbe_ctx *c : s->parts) {
+    hbe_status st = hbe_batch_add(s->batch, c, nsteps, dt);
+    if (st != HBE_OK) return set_err(s->err, st, "%s", s->batch->err.c_str());
+  }
+  // every slab takes the same steps; the halo plan indexes the members in
+  // slab order, so a slab that stops early (non-finite values) ends the run
+  // of all of them
+  std::vector<hbe_ctx *> fin(s->k);
+  hbe_status result = HBE_OK;
+  while (hbe_batch_size(s->batch) > 0) {
+    int nf = 0;
+    hbe_status st = hbe_batch_run(s->batch, fin.data(), s->k, &nf);
+    if (st != HBE_OK) return set_err(s->err, st, "%s", s->batch->err.c_str());
+    for (int i = 0; i < nf && i < s->k; ++i)
+      if (fin[i]->h_desc->status == ST_NONFINITE) result = HBE_NONFINITE;
+    if (nf > 0 && hbe_batch_size(s->batch) > 0) {
+      std::vector<hbe_ctx *> rest(s->batch->members);
+      for (hbe_ctx *c : rest) hbe_batch_remove(s->batch, c);
+      if (result == HBE_OK) result = HBE_NONFINITE;
+    }
+  }
+  if (result != HBE_OK) set_err(s->err, result, "phi became non-finite");
+  return result;
+}
+
+hbe_status hbe_slabs_read_device(hbe_slabs *s, double *d_phi, double *d_psi, double *t) {
+  Range range_("hbe_slabs_read");
+  if (!s) return HBE_EINVAL;
+  const size_t plane = (size_t)s->N * s->N;
+  for (int i = 0; i < s->k; ++i) {
+    hbe_ctx *c = s->parts[i];
+    hbe_status st = sync_ctx(c);
+    if (st != HBE_OK) return set_err(s->err, st, "%s", c->err.c_str());
+    const int sprec = c->prec == HBE_FP64 ? 0 : 1;
+    const bool kahan = is_kahan(c->prec);
+    const int set = (int)(c->h_desc->n_base & 1);
+    if (d_phi)
+      CKX(s->err, launch_unpack(sprec, c->f[F_P0 + set], kahan ? c->f[F_PLO0 + set] : nullptr,
+                                d_phi + s->z0[i] * plane, s->N, c->pitch_s, c->hxs, c->zoff,
+                                s->nz[i], s->stream));
+    if (d_psi)
+      CKX(s->err, launch_unpack(sprec, c->f[F_Q0 + set], kahan ? c->f[F_QLO0 + set] : nullptr,
+                                d_psi + s->z0[i] * plane, s->N, c->pitch_s, c->hxs, c->zoff,
+                                s->nz[i], s->stream));
+  }
+  CKX(s->err, cudaStreamSynchronize(s->stream));
+  if (t) *t = current_t(s->parts[0]);
+  return HBE_OK;
 }
 
 }  // extern "C"

@@ -235,15 +235,15 @@ template <> struct Pair<unsigned short> { using type = unsigned; };
 // overlap: ghost rows are written only at x in [0, N) from interior rows,
 // ghost columns only in interior rows from interior columns.
 template <class E>
-__device__ void wrap_pair(void *va, void *vb, int N, int pitch, int64_t plane, int hx,
-                          long long tid, long long nth) {
+__device__ void wrap_pair(void *va, void *vb, int N, int nzp, int zoff, int pitch, int64_t plane,
+                          int hx, long long tid, long long nth) {
   E *fa = static_cast<E *>(va), *fb = static_cast<E *>(vb);
   const bool two = fb != nullptr;
   using P = typename Pair<E>::type;
   constexpr int VE = 16 / (int)sizeof(E);
   const bool vec = N % VE == 0;
   const int nv = vec ? N / VE : N;                       // row pieces per ghost row
-  const long long nc = (long long)N * N, nr = 4LL * N * nv;
+  const long long nc = (long long)nzp * N, nr = 4LL * nzp * nv;  // nzp planes from zoff
   const long long nu = nc > nr ? nc : nr;
   const bool even = (N & 1) == 0;                        // column pairs aligned
   for (long long u = tid; u < nu; u += nth) {
@@ -253,7 +253,7 @@ __device__ void wrap_pair(void *va, void *vb, int N, int pitch, int64_t plane, i
     if (hr) {
       const int piece = (int)(u % nv);
       const long long r = u / nv;
-      const int z = (int)(r >> 2), g = (int)(r & 3);
+      const int z = (int)(r >> 2) + zoff, g = (int)(r & 3);
       const int dst = g < 2 ? g : N + g, src = g < 2 ? N + g : g;
       const int64_t cb = (int64_t)z * plane + hx + (int64_t)piece * (vec ? VE : 1);
       rs = cb + (int64_t)src * pitch;
@@ -276,7 +276,7 @@ __device__ void wrap_pair(void *va, void *vb, int N, int pitch, int64_t plane, i
     E a[4] = {}, b[4] = {};
     P alo = {}, ahi = {}, blo = {}, bhi = {};
     if (hc) {
-      const int zc = (int)(u / N), y = (int)(u % N);
+      const int zc = (int)(u / N) + zoff, y = (int)(u % N);
       ro = (int64_t)zc * plane + (int64_t)(y + 2) * pitch + hx;
       if (even) {
         alo = *reinterpret_cast<const P *>(fa + ro);
@@ -350,9 +350,46 @@ __global__ void wrap_kernel(Desc *descs, const int *ndesc, int k, int stage) {
   const int pitch = state ? d->pitch_s : d->pitch_g;
   const int64_t plane = state ? d->plane_s : d->plane_g;
   const int hx = 16 / esz;
-  if (esz == 8) wrap_pair<unsigned long long>(fa, fb, N, pitch, plane, hx, tid, nth);
-  else if (esz == 4) wrap_pair<unsigned>(fa, fb, N, pitch, plane, hx, tid, nth);
-  else wrap_pair<unsigned short>(fa, fb, N, pitch, plane, hx, tid, nth);
+  const int nz = d->nz, zoff = d->zoff;
+  if (esz == 8) wrap_pair<unsigned long long>(fa, fb, N, nz, zoff, pitch, plane, hx, tid, nth);
+  else if (esz == 4) wrap_pair<unsigned>(fa, fb, N, nz, zoff, pitch, plane, hx, tid, nth);
+  else wrap_pair<unsigned short>(fa, fb, N, nz, zoff, pitch, plane, hx, tid, nth);
+}
+
+// ---------------------------------------------------------------- z-slab halos
+// The stage pairs read phi, psi (stages 1+2) and phi, psi, G1, G2 (stages 3+4)
+// two planes beyond a slab in z, so after each pair the two planes next to a
+// slab boundary are copied into the neighbour's halo planes: plain 16-byte
+// copies of whole padded planes (their periodic x/y ghosts included, the
+// ghost-copy launch having run before).  Block row y = one transfer.
+__global__ void halo_kernel(const Desc *descs, const HaloCopy *copies, int k, int stage) {
+  const HaloCopy c = copies[blockIdx.y];
+  const Desc &s = descs[c.src];
+  const Desc &d = descs[c.dst];
+  const long long n = s.n_base + k;
+  if (n >= s.n_end || __ldcg(&s.stop_k) <= k) return;  // the step was not taken
+  const bool state = stage == 6;
+  const int es = state ? (s.prec == 0 ? 8 : 4) : (s.prec == 0 ? 8 : (s.prec == 2 ? 2 : 4));
+  const int64_t pb = (state ? s.plane_s : s.plane_g) * es;  // bytes per stored plane
+  const int so = (int)(n & 1) ^ 1;
+  const int fields[2] = {state ? F_P0 + so : F_G1, state ? F_Q0 + so : F_G2};
+  const int64_t units = 2 * pb / 16;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const char *>(s.f[fields[f]]) +
+                                                       c.src_plane * pb);
+    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<char *>(d.f[fields[f]]) + c.dst_plane * pb);
+    for (int64_t i = tid; i < units; i += nth) dst[i] = src[i];
+  }
+}
+
+cudaError_t launch_halo(const Desc *descs, const HaloCopy *copies, int n, int k, int stage,
+                        cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  halo_kernel<<<dim3(32, n), 256, 0, st>>>(descs, copies, k, stage);
+  return cudaGetLastError();
 }
 
 bool stage_needs_wrap(int stage) { return stage == 1 || stage == 2 || stage >= 4; }

@@ -21,6 +21,11 @@ cudaError_t launch_advance(Desc *descs, const int *ndesc, int max_desc, int K, c
 bool stage_needs_wrap(int stage);
 cudaError_t launch_wrap(Desc *descs, const int *ndesc, int max_desc, int k, int stage,
                         int blocks, cudaStream_t st);
+// Halo planes of a z-slab decomposition after stage pair `stage` of step k of
+// a replay: 5 -> G1, G2; 6 -> phi, psi of the new state.  One copy per entry
+// of `copies` (n entries); a copy whose source did not take the step is skipped.
+cudaError_t launch_halo(const Desc *descs, const HaloCopy *copies, int n, int k, int stage,
+                        cudaStream_t st);
 cudaError_t launch_set_run(Desc *d, long long add_steps, double t0, double dt, double thr,
                            int reset, cudaStream_t st);
 cudaError_t launch_signpack(int prec, const void *hi, const void *lo, int N, int pitch, int hx,

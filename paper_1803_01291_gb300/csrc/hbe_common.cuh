@@ -5,8 +5,10 @@
 //   elements before and after it (HX = 16 bytes / element size, so the first
 //   unknown of a row is 16-byte aligned), each z-plane has 2 ghost rows before
 //   and after, and z is not padded:
-//       element (x, y, z) at  z*plane + (y + 2)*pitch + (x + HX),
-//       pitch = round_up(N + 2*HX, HX),  plane = (N + 4)*pitch.
+//       element (x, y, z) at  (z + zoff)*plane + (y + 2)*pitch + (x + HX),
+//       pitch = round_up(N + 2*HX, HX),  plane = (N + 4)*pitch,
+//   zoff = 0 for a whole grid; a z-slab of a decomposed grid stores its nz
+//   planes after zoff = 2 halo planes and before 2 more (Desc::zoff).
 //   Zero-Dirichlet: ghosts stay 0 (the two ghost layers of Eq. BC, zeroed at
 //   allocation and never written).  Periodic: the wrapped copies x in
 //   {-2,-1,N,N+1} and y in {-2,-1,N,N+1} are written by the initial-data
@@ -66,6 +68,11 @@ constexpr int kCoefDoubles = kMaxK * kCoefPerStep + kCoefConsts;
 // n_end, stop_k and status (stage-1 kernels may lower stop_k).
 struct alignas(64) Desc {
   int32_t N, bc, prec, pad0;
+  // z extent of the stored block: nz interior planes starting at storage plane
+  // zoff (a z-slab keeps zoff = 2 halo planes on each side, filled by the halo
+  // exchange); zwrap = 1 wraps z-plane indices (a periodic context stored
+  // whole), else planes outside the storage read as zero
+  int32_t nz, zoff, zwrap, pad2;
   int32_t pitch_s, pitch_g;      // padded row pitch (elements) of state / G fields
   int64_t plane_s, plane_g;      // elements per padded z-plane
   double inv_h2, mu2, lambda;
@@ -81,6 +88,14 @@ struct alignas(64) Desc {
   double *coef;                  // [kCoefDoubles] step coefficients (coef_kernel)
   const CUtensorMap *tmaps;      // [NUM_TMAPS], 64-byte aligned, in device memory
   void *f[NUM_FIELDS];
+};
+
+// One halo transfer of a z-slab decomposition: the 2 stored planes starting
+// at src_plane of batch member src go to the 2 halo planes starting at
+// dst_plane of member dst (whole padded planes, ghost rows and columns
+// included).
+struct HaloCopy {
+  int32_t src, dst, src_plane, dst_plane;
 };
 
 // Work item of a stage launch: one (context, x-y tile, z-chunk) column.

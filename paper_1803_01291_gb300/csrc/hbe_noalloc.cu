@@ -172,6 +172,7 @@ extern "C" hbe_status hbe_step_fp64_noalloc(int N, double L, double mu, double l
   Desc hd;
   memset(&hd, 0, sizeof(hd));
   hd.N = N; hd.bc = bc; hd.prec = HBE_FP64;
+  hd.nz = N; hd.zoff = 0; hd.zwrap = bc == HBE_BC_PERIODIC ? 1 : 0;
   hd.pitch_s = pitch; hd.pitch_g = pitch; hd.plane_s = plane; hd.plane_g = plane;
   hd.inv_h2 = 1.0 / (h * h); hd.mu2 = mu * mu; hd.lambda = lambda;
   hd.t0 = t0; hd.dt = dt;

@@ -306,8 +306,8 @@ __device__ __forceinline__ void produce(const StageParams &prm, uint64_t *full, 
     if (!item_active<S>(d, prm.k, false)) continue;
     const CUtensorMap *tm = d->tmaps;
     for (int t = 0; t < NUM_TMAPS; ++t) tmap_acquire(tm + t);
-    const int N = d->N;
-    const bool periodic = d->bc == 1;
+    const int nz = d->nz, zoff = d->zoff;
+    const bool zwrap = d->zwrap != 0;
     const int set = (int)((d->n_base + prm.k) & 1);
     const CUtensorMap *mp = tm + (S == 5 ? (set ? TM_P_H1_P : TM_P_H0_P) : (set ? TM_P_H1 : TM_P_H0));
     const CUtensorMap *mq = tm + (S == 5 ? (set ? TM_Q_H1_P : TM_Q_H0_P) : (set ? TM_Q_H1 : TM_Q_H0));
@@ -325,7 +325,8 @@ __device__ __forceinline__ void produce(const StageParams &prm, uint64_t *full, 
       unsigned char *base = ring + slot * C::SLOT_BYTES;
       uint64_t *bar = &full[slot];
       int z = z0 - 2 + m;
-      if (periodic) z = (z % N + N) % N;
+      if (zwrap) z = (z % nz + nz) % nz;
+      z += zoff;
       mbar_expect_tx(bar, C::TX_BYTES);
       tma_load_3d(base, mp, bar, x0, y0, z);
       if constexpr (C::NHS == 2) tma_load_3d(base + C::HS_BYTES, mq, bar, x0, y0, z);
@@ -600,7 +601,7 @@ struct Consumer {
   }
 
   struct Item {
-    int N, x, z0, nplanes, set;
+    int N, x, z0, zoff, nplanes, set;
     bool ragged, xok;
     int64_t pitch_s, plane_s, pitch_g, plane_g, row_s, row_g;
     int y0;
@@ -643,7 +644,7 @@ struct Consumer {
     if (m < 4) return;
     // ---- output plane z = z0 + m - 4 (window: z-2 = W(m-4), z-1 = W(m-3),
     // z = W(m-2), z+1 = W(m-1), z+2 = W(m))
-    const int z = it.z0 + m - 4;
+    const int z = it.z0 + m - 4 + it.zoff;  // storage plane of the output
     const unsigned char *b2 = ring + s2 * C::SLOT_BYTES;
     TM R[KN][4][VEC];  // rows ly0-2, ly0-1, ly0+VY, ly0+VY+1 of P at plane z (not INCR)
     if constexpr (!C::INCR) {
@@ -901,6 +902,7 @@ struct Consumer {
       const int x0 = (w.y & 0xffff) * TX;
       it.y0 = (w.y >> 16) * C::TY;
       it.z0 = w.z;
+      it.zoff = d->zoff;
       it.nplanes = w.w + 4;
       it.ragged = x0 + TX > it.N;
       it.x = x0 + self.lx0;
