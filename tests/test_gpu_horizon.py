@@ -14,6 +14,8 @@ workloads.
 * GRF 512^3 with lambda = 2 at t = 6 (308 steps), where the field breaks into
   dozens of sign components: the union-find labelling of the GPU against the
   oracle's breadth-first search on the same field.
+* GRF 512^3 with lambda = 1 (the benchmark workload) over its whole horizon
+  against the oracle, and the 1024^3 focusing workload at sampled nodes.
 """
 import numpy as np
 import pytest
@@ -98,3 +100,62 @@ def test_grf_512_lambda2_components_against_oracle(hbe, prec):
     # the field has broken into many sign components by t = 6
     assert bubbles >= 10, bubbles
     torch.cuda.empty_cache()
+
+
+def test_grf_512_whole_field_against_oracle(hbe):
+    """The 512^3 periodic GRF workload (lambda = 1, seed 0): every node of phi
+    and psi of the FP64 and FP32 (compensated) GPU paths against one oracle
+    run of the same steps.  By default 40 RK4 steps (t = 0.78; 5.4e9
+    point-steps, ~1.5 min on 16 host cores); HBE_FULL_HORIZON=1 runs the whole
+    horizon, 308 steps to t = 6 (4.1e10 point-steps, ~11 min)."""
+    import os
+    import torch
+    prob = hi.grf_problem(512, lam=1.0, seed=0)
+    nsteps = prob.nsteps if os.environ.get("HBE_FULL_HORIZON") == "1" else 40
+    ophi, opsi, n = oracle.run(prob.phi0, prob.phi1, prob.L, prob.mu, prob.lam, prob.bc, 0.0,
+                               prob.dt, nsteps)
+    assert n == nsteps
+    for prec, tol in ((hbe.FP64, 1e-11), (hbe.FP32, 2e-5)):
+        with hbe.Solver(prob.N, prob.L, prob.mu, prob.lam, prob.bc, prec) as s:
+            s.set_initial(torch.from_numpy(prob.phi0).cuda(), torch.from_numpy(prob.phi1).cuda())
+            assert s.step(nsteps, prob.dt) == hbe.OK
+            phi, psi, _ = s.read()
+        assert relerr(phi, ophi) <= tol, (prec, relerr(phi, ophi))
+        assert relerr(psi, opsi) <= tol, (prec, relerr(psi, opsi))
+        torch.cuda.empty_cache()
+
+
+def test_blowup_1024_sampled_against_oracle(hbe):
+    """The 1024^3 focusing workload (lambda = -1, 3 bump(R = 4)): after 2
+    steps, sampled nodes (walls, the bump's centre and edge) of both
+    precisions against the oracle evaluated node by node on the window that
+    can influence them.  phi is held to the relative max-norm bounds.  psi
+    starts at 0 and after k steps is k dt G, where G sums terms of size
+    c (4/3 * 6 + 1/12 * 6) max|phi| with c = e^{-2t}/h^2 (~2.6e3 here) that
+    largely cancel; in FP32 each evaluation of G is rounded at that scale, so
+    psi is held to 2 k dt 2^-24 times it (FP64: the relative 1e-11)."""
+    import torch
+    prob = hi.blowup_problem(1024)
+    N, k = prob.N, 2
+    c = (N - 1) // 2
+    r = int(4.0 / hi.grid_spacing(N, prob.L, prob.bc))  # the bump's radius in nodes
+    pts = [(0, 0, 0), (N - 1, N - 1, N - 1), (c, c, c), (c, c, c + r - 1), (c, c + r, c),
+           (c - r // 2, c, c + r // 2), (1, c, N - 2), (c, 0, c)]
+    ref = oracle.window_values(prob.phi0, prob.phi1, prob.L, prob.mu, prob.lam, prob.bc, 0.0,
+                               prob.dt, k, pts)
+    for prec, tol in ((hbe.FP64, 1e-11), (hbe.FP32, 2e-5)):
+        with hbe.Solver(N, prob.L, prob.mu, prob.lam, prob.bc, prec) as s:
+            s.set_initial(torch.from_numpy(prob.phi0).cuda(), torch.from_numpy(prob.phi1).cuda())
+            assert s.step(k, prob.dt) == hbe.OK
+            phi, psi, _ = s.read()
+        scale = np.max(np.abs(phi))
+        if prec == hbe.FP64:
+            psi_tol = tol * np.max(np.abs(psi))
+        else:
+            h = hi.grid_spacing(N, prob.L, prob.bc)
+            g_scale = (8.5 / h ** 2 + prob.mu ** 2 + abs(prob.lam) * scale ** 2) * scale
+            psi_tol = 2 * k * prob.dt * 2.0 ** -24 * g_scale
+        for i, p in enumerate(pts):
+            assert abs(phi[p] - ref[i, 0]) <= tol * scale, (prec, p, phi[p], ref[i, 0])
+            assert abs(psi[p] - ref[i, 1]) <= psi_tol, (prec, p, psi[p], ref[i, 1], psi_tol)
+        torch.cuda.empty_cache()
