@@ -216,6 +216,22 @@ typedef struct {
 } hbe_analysis_t;
 hbe_status hbe_analysis(hbe_ctx *ctx, double eps, hbe_analysis_t *out);
 
+/* The Laplacian monitor P(t) = e^{-2t} max|Delta_h phi| of Sec. 3 (Example
+ * long-bubble: P(t) -> 0 as the solution approaches its limit) as a
+ * by-product of stepping.  With the monitor on, the stages 1+2 kernel of
+ * every step n also forms max over the grid of |Delta_h phi_n| -- the FD4
+ * Laplacian of the step's starting state, which is that kernel's stage-1
+ * argument -- in the context's arithmetic (FP32 or FP64), and records it;
+ * no extra pass over the fields.  Applies to hbe_step / hbe_step_async with
+ * the fused schedule (1), not to batches.  on: 1 (allocates a history of
+ * 65536 entries, 512 KiB) or 0.  Blocks. */
+hbe_status hbe_set_monitor(hbe_ctx *ctx, int on);
+/* P(t_n) and t_n = t0 + n dt (the current time origin) for the states before
+ * steps n = first .. first + count - 1; those steps must have been taken with
+ * the monitor on, and lie in the last 65472 steps (HBE_EINVAL otherwise).
+ * t may be NULL.  Blocks. */
+hbe_status hbe_monitor_read(hbe_ctx *ctx, int64_t first, int64_t count, double *P, double *t);
+
 /* Raw state (both fields in storage precision, step count, t0, dt) to/from
  * a file; a load into a context of the same N, bc and precision continues
  * bit for bit. */

@@ -20,7 +20,8 @@ EXPORTS = (
     "hbe_workspace_bytes", "hbe_create", "hbe_create_in", "hbe_destroy", "hbe_set_stream",
     "hbe_set_tuning", "hbe_set_schedule", "hbe_variant_info", "hbe_variant_count", "hbe_set_initial",
     "hbe_set_initial_device", "hbe_set_initial_bumps", "hbe_set_stop", "hbe_step", "hbe_step_async", "hbe_sync",
-    "hbe_read", "hbe_read_device", "hbe_profile_stages", "hbe_progress", "hbe_analysis", "hbe_diag", "hbe_save", "hbe_load",
+    "hbe_read", "hbe_read_device", "hbe_profile_stages", "hbe_progress", "hbe_analysis", "hbe_set_monitor",
+    "hbe_monitor_read", "hbe_diag", "hbe_save", "hbe_load",
     "hbe_last_error", "hbe_status_string", "hbe_launch_count", "hbe_batch_create",
     "hbe_batch_destroy", "hbe_batch_add", "hbe_batch_remove", "hbe_batch_run", "hbe_batch_launch",
     "hbe_batch_collect",
@@ -104,6 +105,8 @@ def load() -> ctypes.CDLL:
             "hbe_profile_stages": (I, [P, I64, D, ctypes.POINTER(ctypes.c_float)]),
             "hbe_diag": (I, [P, D, ctypes.POINTER(HbeDiag), P, P]),
             "hbe_analysis": (I, [P, D, ctypes.POINTER(HbeAnalysis)]),
+            "hbe_set_monitor": (I, [P, I]),
+            "hbe_monitor_read": (I, [P, I64, I64, dp, dp]),
             "hbe_save": (I, [P, ctypes.c_char_p]),
             "hbe_load": (I, [P, ctypes.c_char_p]),
             "hbe_last_error": (ctypes.c_char_p, [P]),

@@ -49,6 +49,8 @@ CUtensorMapDataType tm_type(int esize) {
 
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
+constexpr int64_t kMonCap = 65536;  // monitor history: the last 65536 - kMaxK steps
+
 }  // namespace
 
 struct hbe_ctx {
@@ -78,8 +80,10 @@ struct hbe_ctx {
   WorkItem *d_items_p = nullptr;
   int *d_nitems_p = nullptr;
   int nitems_p = 0, items_cap_p = 0, zchunk_p = 0;
-  int grid[6] = {0, 0, 0, 0, 0, 0};
+  int grid[7] = {0, 0, 0, 0, 0, 0, 0};  // [6]: the stages 1+2 kernel with the monitor
   int schedule = 1;  // 0: four one-stage kernels per step; 1: two fused stage pairs
+  bool monitor = false;                 // stages 1+2 record the Laplacian monitor
+  unsigned long long *d_mon = nullptr;  // kMonCap monitor entries (Desc::mon)
   unsigned *d_err = nullptr;
   int K = 8;
   // gexec[n]: graph of n RK4 steps (n = K for the full replays, n < K for the
@@ -283,9 +287,9 @@ hbe_status apply_tuning(hbe_ctx *ctx, int variant, int zchunk) {
   CK(cudaMemcpy(ctx->d_tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice));
   // persistent grid per stage and the two work lists
   int resident = 1 << 30;
-  for (int s = 0; s < 6; ++s) {
+  for (int s = 0; s < 7; ++s) {
     if ((st = persistent_grid(ctx->err, ks[s], ctx->sms, &ctx->grid[s]))) return st;
-    if (s != 4) resident = std::min(resident, ctx->grid[s]);
+    if (s != 4 && s != 6) resident = std::min(resident, ctx->grid[s]);
   }
   const int columns = ((ctx->N + tx - 1) / tx) * ((ctx->N + ty - 1) / ty);
   const int columns_p = ((ctx->N + txp - 1) / txp) * ((ctx->N + typ - 1) / typ);
@@ -308,8 +312,8 @@ hbe_status apply_tuning(hbe_ctx *ctx, int variant, int zchunk) {
     CK(cudaMemcpy(d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(li ? ctx->d_nitems_p : ctx->d_nitems, &n, sizeof(int), cudaMemcpyHostToDevice));
   }
-  for (int s = 0; s < 6; ++s)
-    ctx->grid[s] = std::min(ctx->grid[s], s == 4 ? ctx->nitems_p : ctx->nitems);
+  for (int s = 0; s < 7; ++s)
+    ctx->grid[s] = std::min(ctx->grid[s], (s == 4 || s == 6) ? ctx->nitems_p : ctx->nitems);
   drop_graphs(ctx);
   return HBE_OK;
 }
@@ -386,7 +390,8 @@ hbe_status ensure_graph(hbe_ctx *ctx, int nk) {
   if (ec != cudaSuccess) st = set_err(ctx->err, HBE_ECUDA, "%s", cudaGetErrorString(ec));
   for (int k = 0; k < nk && st == HBE_OK; ++k)
     for (int s = first; s < last && st == HBE_OK; ++s) {
-      st = launch_stage(ctx->err, vt.k[ctx->variant][s], ctx->grid[s], ctx_params(ctx, s, k),
+      const int kid = (s == 4 && ctx->monitor) ? 6 : s;  // stages 1+2 with the monitor
+      st = launch_stage(ctx->err, vt.k[ctx->variant][kid], ctx->grid[kid], ctx_params(ctx, s, k),
                         ctx->cap_stream);
       if (st == HBE_OK && ctx->bc == HBE_BC_PERIODIC && stage_needs_wrap(s + 1)) {
         cudaError_t ew = launch_wrap(ctx->d_desc, ctx->d_one, 1, k, s + 1, wrap_blocks(ctx),
@@ -654,6 +659,7 @@ void hbe_destroy(hbe_ctx *ctx) {
   cudaFree(ctx->d_labels);
   cudaFree(ctx->d_counts);
   cudaFree(ctx->d_part);
+  cudaFree(ctx->d_mon);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
@@ -772,6 +778,7 @@ static hbe_status set_initial_impl(hbe_ctx *ctx, const double *phi0, const doubl
   d.stop_k = kNoStop;
   d.status = ST_RUNNING;
   d.last_done = 0;
+  if (ctx->d_mon) CK(cudaMemset(ctx->d_mon, 0, kMonCap * sizeof(unsigned long long)));
   if ((st = push_desc(ctx)) != HBE_OK) return st;
   CK(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
   ctx->has_state = true;
@@ -839,6 +846,7 @@ hbe_status hbe_set_initial_bumps(hbe_ctx *ctx, int n0, const double *A0, const d
   d.stop_k = kNoStop;
   d.status = ST_RUNNING;
   d.last_done = 0;
+  if (ctx->d_mon) CK(cudaMemset(ctx->d_mon, 0, kMonCap * sizeof(unsigned long long)));
   if ((st = push_desc(ctx)) != HBE_OK) return st;
   CK(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
   ctx->has_state = true;
@@ -1132,6 +1140,50 @@ hbe_status hbe_analysis(hbe_ctx *ctx, double eps, hbe_analysis_t *out) {
   return HBE_OK;
 }
 
+hbe_status hbe_set_monitor(hbe_ctx *ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return HBE_EINVAL;
+  if (ctx->in_batch) return set_err(ctx->err, HBE_ESTATE, "context is in a batch");
+  hbe_status st = sync_ctx(ctx);
+  if (st != HBE_OK) return st;
+  if (on && !ctx->d_mon) {
+    CK(cudaMalloc(&ctx->d_mon, kMonCap * sizeof(unsigned long long)));
+    CK(cudaMemset(ctx->d_mon, 0, kMonCap * sizeof(unsigned long long)));
+  }
+  if ((bool)on != ctx->monitor) drop_graphs(ctx);
+  ctx->monitor = on != 0;
+  ctx->h_desc->mon = on ? ctx->d_mon : nullptr;
+  ctx->h_desc->mon_cap = kMonCap;
+  return push_desc(ctx);
+}
+
+hbe_status hbe_monitor_read(hbe_ctx *ctx, int64_t first, int64_t count, double *P, double *t) {
+  if (!ctx || !P || count < 0) return HBE_EINVAL;
+  if (!ctx->monitor) return set_err(ctx->err, HBE_ESTATE, "the monitor is off");
+  hbe_status st = sync_ctx(ctx);
+  if (st != HBE_OK) return st;
+  const Desc &d = *ctx->h_desc;
+  if (first < 0 || first + count > d.n_base || first < d.n_base - (kMonCap - kMaxK))
+    return set_err(ctx->err, HBE_EINVAL, "steps [%lld, %lld) outside the recorded [%lld, %lld)",
+                   (long long)first, (long long)(first + count),
+                   (long long)std::max<int64_t>(0, d.n_base - (kMonCap - kMaxK)),
+                   (long long)d.n_base);
+  std::vector<unsigned long long> raw((size_t)count);
+  for (int64_t i = 0; i < count;) {
+    const int64_t at = (first + i) % kMonCap, n = std::min(count - i, kMonCap - at);
+    CK(cudaMemcpy(raw.data() + i, ctx->d_mon + at, n * sizeof(unsigned long long),
+                  cudaMemcpyDeviceToHost));
+    i += n;
+  }
+  for (int64_t i = 0; i < count; ++i) {
+    double v;
+    memcpy(&v, &raw[i], sizeof(v));
+    const double tn = d.t0 + (double)(first + i) * d.dt;
+    P[i] = std::exp(-2.0 * tn) * v / (ctx->h * ctx->h);
+    if (t) t[i] = tn;
+  }
+  return HBE_OK;
+}
+
 namespace {
 struct SaveHeader {
   char magic[8];
@@ -1202,6 +1254,7 @@ hbe_status hbe_load(hbe_ctx *ctx, const char *path) {
   Desc &d = *ctx->h_desc;
   d.t0 = hd.t0; d.dt = hd.dt; d.stop_thr = hd.stop_thr;
   d.n_base = hd.n_base; d.n_end = hd.n_base; d.stop_k = kNoStop; d.status = ST_RUNNING;
+  if (ctx->d_mon) CK(cudaMemset(ctx->d_mon, 0, kMonCap * sizeof(unsigned long long)));
   if ((st = push_desc(ctx)) != HBE_OK) return st;
   ctx->has_state = true;
   return HBE_OK;

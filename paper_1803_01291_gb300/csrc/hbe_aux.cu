@@ -166,6 +166,9 @@ __global__ void advance_kernel(Desc *descs, const int *ndesc, int K) {
   }
   d.stop_k = kNoStop;
   for (int k = 0; k < K; ++k) d.maxabs[k] = 0ull;
+  // monitor entries of the steps any next replay may take start from 0
+  if (d.mon)
+    for (int k = 0; k < kMaxK; ++k) d.mon[(d.n_base + k) % d.mon_cap] = 0ull;
 }
 
 // The step coefficients of steps k = 0 .. K-1 of the coming batch (t from the

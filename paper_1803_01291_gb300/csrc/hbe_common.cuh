@@ -86,6 +86,11 @@ struct alignas(64) Desc {
   int32_t pad1;
   unsigned long long *maxabs;    // [kMaxK] max|phi| after step k of the batch (double bits)
   double *coef;                  // [kCoefDoubles] step coefficients (coef_kernel)
+  // Laplacian monitor (stages 1+2 kernel with the monitor): entry n % mon_cap
+  // holds max |h^2 Delta_h phi| of the state before step n as double bits
+  // (atomicMax; the advance kernel zeroes the entries of the coming steps)
+  unsigned long long *mon;
+  int64_t mon_cap;
   const CUtensorMap *tmaps;      // [NUM_TMAPS], 64-byte aligned, in device memory
   void *f[NUM_FIELDS];
 };

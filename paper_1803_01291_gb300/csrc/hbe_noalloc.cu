@@ -53,7 +53,10 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 // metadata layout inside the scratch, after the fields
 constexpr size_t kOffDesc = kFields * kFieldBytes;               // Desc (64-byte aligned)
-constexpr size_t kOffTmaps = kOffDesc + 256;                     // NUM_TMAPS x 128 bytes
+constexpr size_t kOffTmaps = kOffDesc + (sizeof(Desc) + 127) / 128 * 128;  // NUM_TMAPS x 128 bytes
+static_assert(kOffDesc % 64 == 0 && kOffTmaps % 128 == 0 && kOffTmaps >= kOffDesc + sizeof(Desc),
+              "the descriptor must not overlap the tensor maps");
+static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
 constexpr size_t kOffMaxabs = kOffTmaps + NUM_TMAPS * 128;       // kMaxK x 8 bytes
 constexpr size_t kOffErr = kOffMaxabs + kMaxK * 8;               // unsigned
 constexpr size_t kOffCounts = kOffErr + 16;                      // int nitems, int one

@@ -78,7 +78,7 @@ __host__ __device__ constexpr int align128(int b) { return (b + 127) & ~127; }
 __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
-template <class PR, int VEC_, int VY_, int NW_, int BUDGET_, int MINB_, int S_>
+template <class PR, int VEC_, int VY_, int NW_, int BUDGET_, int MINB_, int S_, bool MON_ = false>
 struct StageCfg {
   using TS = typename PR::TS;
   using TG = typename PR::TG;
@@ -134,6 +134,11 @@ struct StageCfg {
   // stage arguments formed by packed FMAs (stages 1+2; the stages 3+4 kernel,
   // which holds the compensated state, spills with them)
   static constexpr bool PCOMB = PACKED && S_ == 5;
+  // stages 1+2 with the Laplacian monitor of Sec. 3: max over the grid of
+  // |Delta_h phi| of the step's starting state (stage 1's argument is phi)
+  static constexpr bool MON = MON_ && S_ == 5;
+  static_assert(!MON_ || S_ == 5, "the monitor rides on the stages 1+2 kernel");
+  static_assert(!MON || INCR || !PACKED, "monitor: packed kernels form the sums part by part");
   static_assert(VEC == 1 || VEC == 2 || VEC == 4, "1, 2 or 4 x points per lane");
   static_assert(VEC * (int)sizeof(TM) <= 16, "lane vector of <= 16 bytes");
   static_assert(HXS >= 2 && HXG >= 2 && HXS % VEC == 0 && HXG % VEC == 0, "halo alignment");
@@ -423,7 +428,8 @@ __device__ __forceinline__ typename C::TM coef_entry(const Desc *d, int kstep, i
 template <class TM>
 __device__ __forceinline__ TM lap_g(TM c43, TM cm12, TM ccen, TM nlam, TM m3, bool diff, TM P0,
                                     TM xm2, TM xm1, TM xp1, TM xp2, TM ym2, TM ym1, TM yp1,
-                                    TM yp2, TM zm2, TM zm1, TM zp1, TM zp2, TM Q) {
+                                    TM yp2, TM zm2, TM zm1, TM zp1, TM zp2, TM Q,
+                                    TM *lap_h2 = nullptr) {
   TM s1, s2;
   if (diff) {
     s1 = ((xm1 - P0) + (xp1 - P0)) + (((ym1 - P0) + (yp1 - P0)) + ((zm1 - P0) + (zp1 - P0)));
@@ -432,6 +438,10 @@ __device__ __forceinline__ TM lap_g(TM c43, TM cm12, TM ccen, TM nlam, TM m3, bo
     s1 = ((xm1 + xp1) + (ym1 + yp1)) + (zm1 + zp1);
     s2 = ((xm2 + xp2) + (ym2 + yp2)) + (zm2 + zp2);
   }
+  // h^2 Delta_h P (Sec. 2.1 weights; the difference form folds the centre in)
+  if (lap_h2)
+    *lap_h2 = diff ? fmaT((TM)(4.0 / 3.0), s1, (TM)(-1.0 / 12.0) * s2)
+                   : fmaT((TM)(4.0 / 3.0), s1, fmaT((TM)(-1.0 / 12.0), s2, (TM)(-7.5) * P0));
   TM g = fmaT(nlam * (P0 * P0), P0, m3 * Q);
   g = fmaT(ccen, P0, g);
   g = fmaT(cm12, s2, g);
@@ -761,6 +771,17 @@ struct Consumer {
                                        f2(k.m3), P0[kk][jp], s1, s2, Q);
             res[kk][j] = g.x;
             res[kk][j + 1] = g.y;
+            if constexpr (C::MON) {
+              if (kk == 0) {
+                // h^2 Delta_h phi at the two points; the largest |.| over valid points
+                const float2 lap = __ffma2_rn(f2(4.0f / 3.0f), s1,
+                                              __fmul2_rn(f2(-1.0f / 12.0f), s2));
+                const bool ok = it.xok && it.y0 + ly < it.N;
+                const float a0 = (ok && it.x + j < it.N) ? fabsf(lap.x) : 0.f;
+                const float a1 = (ok && it.x + j + 1 < it.N) ? fabsf(lap.y) : 0.f;
+                run_max = fmaxf(run_max, fmaxf(a0, a1));
+              }
+            }
           }
         }
       } else if constexpr (C::PACKED) {
@@ -798,11 +819,18 @@ struct Consumer {
             TM Q;
             if (kk == 0) Q = (S == 1 || S == 5) ? qS[j] : fmaT(k.q0, X[j], qS[j]);
             else Q = fmaT(k.q1, res[0][j], qS[j]);
+            TM lap = (TM)0;
             res[kk][j] = lap_g(k.c43[kk], k.cm12[kk], k.ccen[kk], k.nlam, k.m3, C::DIFF, c[kk][j],
                                e[kk][j], e[kk][j + 1], e[kk][j + 3], e[kk][j + 4], Pz(kk, r - 2, j),
                                Pz(kk, r - 1, j), Pz(kk, r + 1, j), Pz(kk, r + 2, j),
                                win[WM4][kk][r][j], win[WM3][kk][r][j], win[WM1][kk][r][j],
-                               win[W0][kk][r][j], Q);
+                               win[W0][kk][r][j], Q, (C::MON && kk == 0) ? &lap : nullptr);
+            if constexpr (C::MON) {
+              if (kk == 0 && it.xok && y < it.N && it.x + j < it.N) {
+                const TM a = lap < (TM)0 ? -lap : lap;
+                run_max = a > run_max ? a : run_max;
+              }
+            }
           }
         }
       }
@@ -974,11 +1002,13 @@ struct Consumer {
         for (; ok && m < it.nplanes; ++m) ok = step(std::integral_constant<int, -1>{}, m);
       }
       if (!ok) return;
-      if constexpr (S == 4 || S == 6) {
+      if constexpr (S == 4 || S == 6 || C::MON) {
         double v = (double)run_max;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (lane_ == 0) atomicMax(d->maxabs + prm.k, (unsigned long long)__double_as_longlong(v));
+        unsigned long long *dst = d->maxabs + prm.k;
+        if constexpr (C::MON) dst = d->mon + (n % d->mon_cap);  // the step's monitor entry
+        if (lane_ == 0) atomicMax(dst, (unsigned long long)__double_as_longlong(v));
       }
     }
   }

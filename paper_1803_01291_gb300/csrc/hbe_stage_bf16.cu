@@ -19,6 +19,7 @@ void add(VariantTable &t) {
   k[3] = info<StageCfg<PR, V, VY, NW, B, MB, 4>>();
   k[4] = info<StageCfg<PR, V, VY, NW5, B, MB, 5>>();
   k[5] = info<StageCfg<PR, V, VY, NW, B, MB, 6>>();
+  k[6] = info<StageCfg<PR, V, VY, NW5, B, MB, 5, true>>();
 }
 }  // namespace
 

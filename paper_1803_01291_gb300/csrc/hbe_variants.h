@@ -20,7 +20,7 @@ struct VariantTable {
   int count;
   // [variant][0..3] one RK stage per launch; [4] stages 1+2; [5] stages 3+4 + combine.
   // Every kernel of a variant has the same tile except [4], which may be taller.
-  KernelInfo k[kMaxVariants][6];
+  KernelInfo k[kMaxVariants][7];  // [6]: [4] with the Laplacian monitor
 };
 
 const VariantTable &variants_fp64();

@@ -228,6 +228,21 @@ class Solver:
         self._chk(self.lib.hbe_analysis(self._ctx, eps, ctypes.byref(out)))
         return {f: getattr(out, f) for f, _ in _lib.HbeAnalysis._fields_}
 
+    def set_monitor(self, on: bool = True):
+        """Record the Laplacian monitor P(t_n) of every step's starting state
+        from the stages 1+2 kernel (Sec. 3)."""
+        self._chk(self.lib.hbe_set_monitor(self._ctx, int(bool(on))))
+
+    def monitor(self, first: int, count: int):
+        """(P, t) arrays of the monitor for the states before steps first ..
+        first + count - 1."""
+        P = np.empty(count)
+        t = np.empty(count)
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._chk(self.lib.hbe_monitor_read(self._ctx, int(first), int(count),
+                                            P.ctypes.data_as(dp), t.ctypes.data_as(dp)))
+        return P, t
+
     def save(self, path: str):
         self._chk(self.lib.hbe_save(self._ctx, path.encode()))
 

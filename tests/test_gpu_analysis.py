@@ -83,3 +83,44 @@ def test_periodic_monitor_at_the_wrap(hbe, prec):
         a = s.analysis()
     lap = oracle.laplacian(phi, h, 1)
     assert math.isclose(a["laplacian_monitor"], math.exp(-2 * t) * np.max(np.abs(lap)), rel_tol=1e-12)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_monitor_from_the_stage_pass(hbe, prec, bc):
+    """P(t_n) recorded by the stages 1+2 kernel while stepping (11 steps: a full
+    replay of 8 and one of 3) against e^{-2 t_n} max|Delta_h phi_n| of the
+    oracle's Laplacian on the GPU's own state before each step, and stepping
+    with the monitor on leaves the state bitwise unchanged."""
+    N, L, mu, lam, n = 36, 10.0, 1.5, 1.0, 11
+    rng = np.random.default_rng(40 + bc)
+    from scipy import ndimage
+    mode = "wrap" if bc == 1 else "constant"
+    phi0 = ndimage.gaussian_filter(rng.standard_normal((N, N, N)), 2.0, mode=mode) * 3
+    phi1 = ndimage.gaussian_filter(rng.standard_normal((N, N, N)), 2.0, mode=mode)
+    h = hi.grid_spacing(N, L, bc)
+    dt = h / 4
+    # reference: the state before each step, stepped one at a time without the monitor
+    want = []
+    with hbe.Solver(N, L, mu, lam, bc, prec) as s:
+        s.set_initial(phi0, phi1, 0.1)
+        for i in range(n):
+            phi, _, t = s.read(psi=False)
+            lap = oracle.laplacian(phi, h, bc)
+            want.append(math.exp(-2.0 * t) * np.max(np.abs(lap)))
+            s.step(1, dt)
+        ref_end = s.read(psi=False)[0]
+    with hbe.Solver(N, L, mu, lam, bc, prec) as s:
+        s.set_initial(phi0, phi1, 0.1)
+        s.set_monitor(True)
+        assert s.step(n, dt) == hbe.OK
+        P, t = s.monitor(0, n)
+        end = s.read(psi=False)[0]
+        with pytest.raises(hbe.HBEError):
+            s.monitor(0, n + 1)  # step n has not been taken
+    assert np.array_equal(end, ref_end)
+    assert np.allclose(t, 0.1 + np.arange(n) * dt, rtol=0, atol=1e-14)
+    # FP64: the same Laplacian to rounding; FP32 family: the stencil of phi's
+    # FP32 (high) part in FP32 arithmetic, against the full state in FP64
+    tol = 1e-12 if prec == 0 else 2e-5
+    assert np.max(np.abs(P - want) / np.array(want)) <= tol, (P, want)
