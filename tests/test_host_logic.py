@@ -192,13 +192,23 @@ def test_request_larger_than_the_budget_is_refused(server_mod):
         srv.run(_requests(serve, [64]), realtime=False)
 
 
-def test_small_grids_get_the_smallest_tile(server_mod):
+def test_every_size_shares_one_variant_by_default(server_mod):
+    """Without a tuning callback all members use variant 0, so a batch graph
+    launches one pair of stage kernels per step; a callback overrides it."""
     serve = server_mod
     srv = serve.Server(_lib.FP32, K=4, hbm_budget=1 << 40)
-    vs = serve.variants(_lib.FP32)
-    small = srv._default_variant(64)
-    assert vs[small]["tile_x"] * vs[small]["tile_y"] == min(v["tile_x"] * v["tile_y"] for v in vs)
-    assert srv._default_variant(256) == 0
+    assert {srv._default_variant(N) for N in (32, 64, 192, 256)} == {0}
+    reqs = _requests(serve, [32, 64])
+    srv.run(reqs, realtime=False)
+    srv2 = serve.Server(_lib.FP32, K=4, hbm_budget=1 << 40, tuning=lambda N, p: (3, 0))
+    seen = []
+    orig = FakeSolver.set_tuning
+    FakeSolver.set_tuning = lambda self, v, zc: seen.append(v)
+    try:
+        srv2.run(_requests(serve, [32]), realtime=False)
+    finally:
+        FakeSolver.set_tuning = orig
+    assert seen == [3]
 
 
 # ---------------------------------------------------------------- request stream
