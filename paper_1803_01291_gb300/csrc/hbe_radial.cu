@@ -113,6 +113,23 @@ __device__ __forceinline__ float2 g_pair(const float (&E)[V + 4], int j, float2 
 // adjacent lanes by shuffles and, across warps, from the `edge` exchange in
 // shared memory, behind one block barrier per stage.  TH: most threads a
 // block, MINB: CTAs per SM the registers must allow.
+// out[j] = a * x[j] + y[j] for the V owned nodes, each with one rounding; two
+// nodes per packed instruction in FP32 (the same bits as the scalar FMA)
+template <typename T, int V>
+__device__ __forceinline__ void axpy(T (&out)[V], T a, const T (&x)[V], const T (&y)[V]) {
+  if constexpr (std::is_same<T, float>::value && V % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < V; j += 2) {
+      const float2 r = __ffma2_rn(p2(a), p2(x[j], x[j + 1]), p2(y[j], y[j + 1]));
+      out[j] = r.x;
+      out[j + 1] = r.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < V; ++j) out[j] = fm(a, x[j], y[j]);
+  }
+}
+
 template <typename T, int V, int TH, int MINB>
 __global__ void __launch_bounds__(TH, MINB) radial_kernel(Args a) {
   static_assert(V >= 3, "the origin mirror reads nodes 1 and 2 from thread 0");
@@ -216,10 +233,16 @@ __global__ void __launch_bounds__(TH, MINB) radial_kernel(Args a) {
         for (int j = 0; j < V; j += 2) {
           const float2 g = g_pair<V>(E, j, p2(w[j], w[j + 1]), p2(Qv[j], Qv[j + 1]), c,
                                      p2(A[j], A[j + 1]), mu2, lam);
-          out[j] = i0 + j < n ? g.x : T(0);
-          out[j + 1] = i0 + j + 1 < n ? g.y : T(0);
+          out[j] = g.x;
+          out[j + 1] = g.y;
         }
         if (tid == 0) out[0] = rhs_g(Qv[0], c, lap(E, 0), A[0], mu2, lam);  // the origin
+        // nodes at or beyond the wall keep 0 (only the thread that holds the wall)
+        if (i0 + V > n) {
+#pragma unroll
+          for (int j = 0; j < V; ++j)
+            if (i0 + j >= n) out[j] = T(0);
+        }
       } else {
 #pragma unroll
         for (int j = 0; j < V; ++j)
@@ -230,39 +253,41 @@ __global__ void __launch_bounds__(TH, MINB) radial_kernel(Args a) {
     // stage 1: argument p -> G1
     eval(g1, p, q, c1);
     // stage 2: argument P2 = p + dt/2 q, Q2 = q + dt/2 G1 -> G2
-#pragma unroll
-    for (int j = 0; j < V; ++j) P[j] = fm(hdt, q[j], p[j]);
-    exchange(P, E, 0);
-#pragma unroll
-    for (int j = 0; j < V; ++j) Qs[j] = fm(hdt, g1[j], q[j]);
-    eval(g2, P, Qs, c2);
+    T H[V];  // p + dt/2 q, shared by stages 2 and 3
+    axpy(H, hdt, q, p);
+    exchange(H, E, 0);
+    axpy(Qs, hdt, g1, q);
+    eval(g2, H, Qs, c2);
     // stage 3: argument P3 = p + dt/2 q + dt^2/4 G1, Q3 = q + dt/2 G2 -> G3
-#pragma unroll
-    for (int j = 0; j < V; ++j) P[j] = fm(qdt2, g1[j], fm(hdt, q[j], p[j]));
+    axpy(P, qdt2, g1, H);
     exchange(P, E, 0);
-#pragma unroll
-    for (int j = 0; j < V; ++j) Qs[j] = fm(hdt, g2[j], q[j]);
+    axpy(Qs, hdt, g2, q);
     eval(g3, P, Qs, c3);
     // stage 4: argument P4 = p + dt q + dt^2/2 G2, Q4 = q + dt G3 -> G4; RK4 combine
-#pragma unroll
-    for (int j = 0; j < V; ++j) P[j] = fm(hdt2, g2[j], fm(dt, q[j], p[j]));
+    T D[V];  // p + dt q, shared by stage 4 and the combine
+    axpy(D, dt, q, p);
+    axpy(P, hdt2, g2, D);
     exchange(P, E, 0);
     T lmax = T(0);
-    T g4v[V];
-#pragma unroll
-    for (int j = 0; j < V; ++j) Qs[j] = fm(dt, g3[j], q[j]);
+    T g4v[V] = {};  // 0 at and beyond the wall (the FP64 evaluation skips those nodes)
+    axpy(Qs, dt, g3, q);
     eval(g4v, P, Qs, c4);
+    // every field is 0 at and beyond the wall, so the combine keeps it 0 there
+    T s3[V], s4[V], s23[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) {
-      if (i0 + j < n) {
-        const T g4 = g4v[j];
-        const T s3 = g1[j] + g2[j] + g3[j];
-        p[j] = fm(sdt2, s3, fm(dt, q[j], p[j]));
-        q[j] = fm(sdt, fm(T(2), g2[j] + g3[j], g1[j] + g4), q[j]);
-        const T m = fabs(p[j]);
-        if (!(m <= m) || isinf(m)) bad = 1;  // NaN or infinite
-        lmax = tmax(lmax, m);
-      }
+      s3[j] = g1[j] + g2[j] + g3[j];
+      s23[j] = g2[j] + g3[j];
+      s4[j] = g1[j] + g4v[j];
+    }
+    axpy(p, sdt2, s3, D);
+    axpy(s23, T(2), s23, s4);
+    axpy(q, sdt, s23, q);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      const T m = fabs(p[j]);
+      if (!(m <= m) || isinf(m)) bad = 1;  // NaN or infinite
+      lmax = tmax(lmax, m);
     }
     if (bad) atomicOr(&sh.any_nonfinite, 1);
     flag = bad || (a.stop > 0.0 && (double)lmax > a.stop);
