@@ -442,8 +442,8 @@ __device__ __forceinline__ TM lap_g(TM c43, TM cm12, TM ccen, TM nlam, TM m3, bo
   if (lap_h2)
     *lap_h2 = diff ? fmaT((TM)(4.0 / 3.0), s1, (TM)(-1.0 / 12.0) * s2)
                    : fmaT((TM)(4.0 / 3.0), s1, fmaT((TM)(-1.0 / 12.0), s2, (TM)(-7.5) * P0));
-  TM g = fmaT(nlam * (P0 * P0), P0, m3 * Q);
-  g = fmaT(ccen, P0, g);
+  // reaction and centre terms as (ccen - lambda P0^2) P0 - 3 Q
+  TM g = fmaT(fmaT(nlam, P0 * P0, ccen), P0, m3 * Q);
   g = fmaT(cm12, s2, g);
   return fmaT(c43, s1, g);
 }
@@ -461,8 +461,7 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
 __device__ __forceinline__ float2 lap_tail2(float2 c43, float2 cm12, float2 ccen, float2 nlam,
                                            float2 m3, float2 P0, float2 s1, float2 s2,
                                            float2 Q) {
-  float2 g = __ffma2_rn(__fmul2_rn(nlam, __fmul2_rn(P0, P0)), P0, __fmul2_rn(m3, Q));
-  g = __ffma2_rn(ccen, P0, g);
+  float2 g = __ffma2_rn(__ffma2_rn(nlam, __fmul2_rn(P0, P0), ccen), P0, __fmul2_rn(m3, Q));
   g = __ffma2_rn(cm12, s2, g);
   return __ffma2_rn(c43, s1, g);
 }
@@ -859,7 +858,8 @@ struct Consumer {
 #pragma unroll
         for (int j = 0; j < VEC; ++j) {
           const TM dp = fmaT(k.b6, (g1[j] + g2[j]) + g3[j], k.dt * qS[j]);
-          const TM dq = k.d6 * ((g1[j] + G4[j]) + (TM)2 * (g2[j] + g3[j]));
+          // 2 x is exact, so the FMA rounds 2 (g2 + g3) + (g1 + G4) once, as before
+          const TM dq = k.d6 * fmaT((TM)2, g2[j] + g3[j], g1[j] + G4[j]);
           if constexpr (C::KAHAN) {
             two_sum(pS[j], dp + lp[j], pn[j], pl[j]);
             two_sum(qS[j], dq + lq[j], qn[j], ql[j]);
