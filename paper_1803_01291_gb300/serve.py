@@ -120,18 +120,35 @@ class Server:
         self.in_use = 0
         self._live: Dict[int, tuple] = {}
         self._side = None  # stream of the retirement work (diagnostics, reads)
+        self._tuned: Dict[tuple, tuple] = {}  # (N, bc) -> (variant, zchunk)
 
     def need_bytes(self, req: SolveRequest) -> int:
         return workspace_bytes(req.N, req.bc, self.prec)
 
     def _default_variant(self, N: int) -> int:
-        """Tile variant of a member when no tuning is given: variant 0 for
-        every size.  One variant means one pair of stage launches per step for
-        the whole batch; measured on the 256-request stream, that beat giving
+        """Tile variant of a member when neither a tuning callback nor the
+        autotuner's cache gives one: variant 0 for every size.  One variant
+        means one pair of stage launches per step for the whole batch;
+        measured on the 256-request stream, that beat giving
         grids below 256^3 the smallest tile (closed-loop capacity 70.1 against
         66.7 Gpoint-steps/s, p99 latency 0.277 against 0.280 s) now that the
         stages 1+2 kernel of variant 0 runs 16 warps on its own tile."""
         return 0
+
+    def _cached_tuning(self, N: int, bc: int) -> tuple:
+        """(variant, z-chunk) the autotuner recorded for this size, boundary and
+        precision (autotune.py's cache), else variant 0 with the automatic
+        z-chunk.  Members always run the fused schedule."""
+        key = (N, bc)
+        if key not in self._tuned:
+            try:
+                from . import autotune
+                e = autotune.load_cache().get(autotune._key(N, bc, self.prec))
+            except Exception:
+                e = None
+            self._tuned[key] = ((int(e["variant"]), int(e["zchunk"])) if e
+                                else (self._default_variant(N), 0))
+        return self._tuned[key]
 
     def _out_of_memory(self, e: Exception) -> bool:
         if isinstance(e, _lib.HBEError):
@@ -143,9 +160,9 @@ class Server:
         s = Solver(req.N, req.L, req.mu, req.lam, req.bc, self.prec)
         if self.tuning is not None:
             v, zc = self.tuning(req.N, self.prec)
-            s.set_tuning(v, zc)
         else:
-            s.set_tuning(self._default_variant(req.N), 0)
+            v, zc = self._cached_tuning(req.N, req.bc)
+        s.set_tuning(v, zc)
         if req.bumps is not None:
             s.set_initial_bumps(req.bumps)
         else:

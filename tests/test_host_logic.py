@@ -211,6 +211,25 @@ def test_every_size_shares_one_variant_by_default(server_mod):
     assert seen == [3]
 
 
+def test_server_uses_the_autotuner_cache(server_mod, tmp_path, monkeypatch):
+    """Sizes the autotuner has tuned get its (variant, z-chunk); others variant 0."""
+    serve = server_mod
+    from paper_1803_01291_gb300 import autotune
+    monkeypatch.setenv("HBE_AUTOTUNE_CACHE", str(tmp_path / "c.json"))
+    monkeypatch.setattr(autotune, "_gpu_name", lambda: "test-gpu")
+    cache = {autotune._key(48, 0, _lib.FP32): {"variant": 2, "zchunk": 16, "schedule": 0}}
+    autotune.save_cache(cache)
+    seen = []
+    orig = FakeSolver.set_tuning
+    FakeSolver.set_tuning = lambda self, v, zc: seen.append((self.N, v, zc))
+    try:
+        srv = serve.Server(_lib.FP32, K=4, hbm_budget=1 << 40)
+        srv.run(_requests(serve, [48, 64, 48]), realtime=False)
+    finally:
+        FakeSolver.set_tuning = orig
+    assert sorted(seen) == [(48, 2, 16), (48, 2, 16), (64, 0, 0)]
+
+
 # ---------------------------------------------------------------- request stream
 def test_request_stream_is_seeded_and_in_range():
     a = hi.request_stream(50, seed=3)
