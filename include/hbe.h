@@ -281,9 +281,13 @@ int hbe_radial_max_n(int prec);
  * prec: HBE_FP64, or HBE_FP32 (state and arithmetic in binary32, t and the
  * stage coefficients formed in binary64).  4 <= n <= hbe_radial_max_n(prec).
  * stop = 0 disables the threshold; non-finite values always end a problem.
- * One CTA per problem integrates all steps on chip.  Asynchronous on `stream`
- * (cudaStream_t, NULL = legacy default); returns HBE_EINVAL for bad arguments
- * (nothing is launched) and HBE_ECUDA if the launch fails. */
+ * One CTA per problem integrates all steps on chip; the stage coefficients
+ * e^{-2 t_s} / dr^2, the same for every problem, are tabled once per call in
+ * a stream-ordered temporary of 4 entries a step (16 bytes a step in FP32,
+ * 32 in FP64), freed on the stream after the solve.
+ * Asynchronous on `stream` (cudaStream_t, NULL = legacy default); returns
+ * HBE_EINVAL for bad arguments (nothing is launched), HBE_ENOMEM if the table
+ * cannot be allocated and HBE_ECUDA if the launch fails. */
 hbe_status hbe_radial_run(int batch, int n, double R, const double *d_mu, const double *d_lambda,
                           const double *d_phi0, const double *d_phi1, double t0, double dt,
                           int64_t nsteps, int prec, int record_every, double stop, double eps,

@@ -16,8 +16,11 @@
 // arguments in registers; the two neighbours on each side come from the
 // adjacent lanes by warp shuffles and, at warp boundaries, through a small
 // exchange in shared memory, so a step costs four block barriers and no
-// global-memory traffic.  The stage coefficients e^{-2 t_s} / dr^2 are computed
-// in double precision, 64 steps at a time, into shared memory.
+// global-memory traffic beyond 16 bytes of stage coefficients a step.  The
+// coefficients e^{-2 t_s} / dr^2 are the same for every problem of the batch:
+// a small kernel forms them in double precision once per step and stage
+// (t_n = t0 + n dt) and rounds them to the solver's type; each CTA copies
+// them into shared memory 64 steps at a time.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,6 +34,7 @@ namespace hbe_radial {
 
 constexpr int kMaxThreads = 512;
 constexpr int kCoefChunk = 64;  // steps whose stage coefficients are tabled at once
+static_assert((kCoefChunk & (kCoefChunk - 1)) == 0, "a power of two");
 
 struct Args {
   int n;
@@ -44,11 +48,25 @@ struct Args {
   double *phi, *psi, *records;
   int64_t *steps;
   int32_t *status;
+  const void *ctab;  // [nsteps][4] stage coefficients, in the solver's type
 };
+
+// ctab[4 n + s] = e^{-2 t_s} / dr^2 for stage s of step n (stage times t_n,
+// t_n + dt/2, t_n + dt/2, t_n + dt; t_n = t0 + n dt), formed in double.
+template <typename T>
+__global__ void radial_coef_kernel(T *ctab, double t0, double dt, double inv_dr2, int64_t nsteps) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 4 * nsteps;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(e & 3);
+    const double t = t0 + (double)(e >> 2) * dt;
+    const double ts = s == 0 ? t : (s == 3 ? t + dt : t + dt / 2);
+    ctab[e] = T(exp(-2.0 * ts) * inv_dr2);
+  }
+}
 
 template <typename T>
 struct Shared {
-  double coef[kCoefChunk][4];
+  T coef[kCoefChunk][4];  // e^{-2 t_s} / dr^2 formed in double, rounded once to T
   // stage-argument values at the ends of each warp's run of nodes, double
   // buffered by stage: [buffer][0: last two nodes, 1: first two][warp][2]
   T edge[2][2][kMaxThreads / 32][2];
@@ -182,22 +200,26 @@ __global__ void __launch_bounds__(TH, MINB) radial_kernel(Args a) {
     return lap_dr2(E[j], E[j + 1], E[j + 2], E[j + 3], E[j + 4], tid == 0 && j == 0, w[j]);
   };
 
+  // (double)x > stop for a T value x  <=>  x > stop rounded toward -inf in T
+  const bool use_stop = a.stop > 0.0;
+  T stop_t;
+  if constexpr (std::is_same<T, float>::value) stop_t = __double2float_rd(a.stop);
+  else stop_t = a.stop;
   int64_t k = 0;
   int status = 0, flag = 0, bad = 0;
   int64_t pending = 0;  // 1 + index of a record whose partial results await combining
-  const double inv_dr2 = 1.0 / (a.dr * a.dr);
+  // steps to the next record and records taken (no 64-bit division per step)
+  int rec_left = a.record_every;
+  int64_t rec_done = 0;
   T E[V + 4], P[V];
   for (;; ++k) {
-    const int kc = (int)(k % kCoefChunk);
+    const int kc = (int)(k & (kCoefChunk - 1));  // k >= 0, kCoefChunk a power of 2
     if (kc == 0 && k < a.nsteps) {
-      // table e^{-2 t_s} / dr^2 for the next steps (t_n = t0 + n dt, Sec. 2.1);
-      // the barrier of the exchange below publishes it
-      for (int e = tid; e < 4 * kCoefChunk; e += blockDim.x) {
-        const int s = e & 3, kk = e >> 2;
-        const double t = a.t0 + (double)(k + kk) * a.dt;
-        const double ts = s == 0 ? t : (s == 3 ? t + a.dt : t + a.dt / 2);
-        sh.coef[kk][s] = exp(-2.0 * ts) * inv_dr2;
-      }
+      // the next steps' e^{-2 t_s} / dr^2 (t_n = t0 + n dt, Sec. 2.1) from the
+      // table; the barrier of the exchange below publishes them
+      const T *ctab = static_cast<const T *>(a.ctab);
+      for (int e = tid; e < 4 * kCoefChunk; e += blockDim.x)
+        if (4 * k + e < 4 * a.nsteps) (&sh.coef[0][0])[e] = ctab[4 * k + e];
     }
     // stage 1 exchange; its barrier also ends step k - 1 (stop rule, records)
     const int any = exchange(p, E, flag);
@@ -223,8 +245,7 @@ __global__ void __launch_bounds__(TH, MINB) radial_kernel(Args a) {
       break;
     }
     if (k >= a.nsteps) break;
-    const T c1 = T(sh.coef[kc][0]), c2 = T(sh.coef[kc][1]), c3 = T(sh.coef[kc][2]),
-            c4 = T(sh.coef[kc][3]);
+    const T c1 = sh.coef[kc][0], c2 = sh.coef[kc][1], c3 = sh.coef[kc][2], c4 = sh.coef[kc][3];
     // G of every owned node from the stage argument (in E and A) and the point
     // argument Q; nodes at or beyond n keep 0
     auto eval = [&](T (&out)[V], const T (&A)[V], const T (&Qv)[V], T c) {
@@ -290,9 +311,10 @@ __global__ void __launch_bounds__(TH, MINB) radial_kernel(Args a) {
       lmax = tmax(lmax, m);
     }
     if (bad) atomicOr(&sh.any_nonfinite, 1);
-    flag = bad || (a.stop > 0.0 && (double)lmax > a.stop);
-    const int64_t done = k + 1;
-    if (a.nrec > 0 && done % a.record_every == 0 && done / a.record_every <= a.nrec) {
+    flag = bad || (use_stop && lmax > stop_t);
+    if (rec_done < a.nrec && --rec_left == 0) {  // after steps record_every, 2 record_every, ...
+      rec_left = a.record_every;
+      ++rec_done;
       // partial max|phi| and strict sign changes (|phi| <= eps ignored) of this
       // thread's run of nodes; combined by thread 0 after the next barrier
       T m = lmax;
@@ -312,7 +334,7 @@ __global__ void __launch_bounds__(TH, MINB) radial_kernel(Args a) {
       sh.first[tid] = f;
       sh.last[tid] = l;
       sh.changes[tid] = c;
-      pending = done / a.record_every;
+      pending = rec_done;
     }
   }
 
@@ -331,11 +353,24 @@ __global__ void __launch_bounds__(TH, MINB) radial_kernel(Args a) {
 }
 
 template <typename T, int V, int TH, int MINB>
-cudaError_t launch(const Args &a, int batch, cudaStream_t st) {
+cudaError_t launch(Args a, int batch, cudaStream_t st) {
   const int threads = std::max(32, ((a.n + V - 1) / V + 31) / 32 * 32);
   if (threads > TH) return cudaErrorInvalidConfiguration;
+  // the coefficient table lives for this launch only (stream-ordered memory)
+  T *tab = nullptr;
+  if (a.nsteps > 0) {
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&tab),
+                                    (size_t)a.nsteps * 4 * sizeof(T), st);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = std::min<int64_t>((4 * a.nsteps + 255) / 256, 4096);
+    radial_coef_kernel<T><<<(int)blocks, 256, 0, st>>>(tab, a.t0, a.dt, 1.0 / (a.dr * a.dr),
+                                                       a.nsteps);
+  }
+  a.ctab = tab;
   radial_kernel<T, V, TH, MINB><<<batch, threads, 0, st>>>(a);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (tab) cudaFreeAsync(tab, st);
+  return e;
 }
 
 }  // namespace hbe_radial
@@ -384,5 +419,9 @@ extern "C" hbe_status hbe_radial_run(int batch, int n, double R, const double *d
     e = n <= 2048 ? launch<double, 8, 256, 1>(a, batch, st) : launch<double, 8, 512, 1>(a, batch, st);
   else
     e = n <= 2048 ? launch<float, 8, 256, 2>(a, batch, st) : launch<float, 8, 512, 1>(a, batch, st);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return HBE_ENOMEM;
+  }
   return e == cudaSuccess ? HBE_OK : HBE_ECUDA;
 }
