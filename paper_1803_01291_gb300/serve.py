@@ -131,8 +131,8 @@ class Server:
         means one pair of stage launches per step for the whole batch;
         measured on the 256-request stream, that beat giving
         grids below 256^3 the smallest tile (closed-loop capacity 70.1 against
-        66.7 Gpoint-steps/s, p99 latency 0.277 against 0.280 s) now that the
-        stages 1+2 kernel of variant 0 runs 16 warps on its own tile."""
+        66.7 Gpoint-steps/s, p99 latency 0.277 against 0.280 s) once the
+        stages 1+2 kernels had been made leaner."""
         return 0
 
     def _cached_tuning(self, N: int, bc: int) -> tuple:
