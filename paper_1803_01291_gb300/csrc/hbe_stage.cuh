@@ -102,7 +102,6 @@ struct StageCfg {
   // interior tiles of the fields read at the point only
   static constexpr int NHS = (S == 1) ? 1 : 2;                                  // p [, q]
   static constexpr int NHG = (S == 3 || S == 4) ? 1 : (S == 6 ? 2 : 0);         // G1 | G2 | G1, G2
-  static constexpr int NIS = (S == 1) ? 1 : (((S == 4 || S == 6) && KAHAN) ? 2 : 0);
   static constexpr int NIG = (S == 1 || S >= 5) ? 0 : ((S == 4) ? 2 : 1);       // G1 | G2 | G1, G3
   static constexpr int HS_RAW = BY * BXS * (int)sizeof(TS);
   static constexpr int HG_RAW = BY * BXG * (int)sizeof(TG);
@@ -110,16 +109,36 @@ struct StageCfg {
   static constexpr int IG_RAW = TY * TX * (int)sizeof(TG);
   static constexpr int HS_BYTES = align128(HS_RAW), HG_BYTES = align128(HG_RAW);
   static constexpr int IS_BYTES = align128(IS_RAW), IG_BYTES = align128(IG_RAW);
+  static constexpr int HEADER = 384;  // 2 x 16 mbarriers, flags, 2 x 4 mbarriers
+  static constexpr int ring_of(int budget, int slot) { return cmax(4, cmin(16, budget / slot)); }
+  // Stages 3+4 read the compensation terms at the output point only.  A slot
+  // is held for three plane steps (its tiles feed the stencils of planes m,
+  // m+1 and m+2), so where a ring with those tiles inside would hold at most 5
+  // slots (two planes in flight), they get a ring of their own of 3 slots, each
+  // held for one step: the main ring then holds one plane more.  Deeper rings
+  // keep them inside, where their lead is that of the main ring.
+  static constexpr int MAIN_BYTES = NHS * HS_BYTES + NHG * HG_BYTES + NIG * IG_BYTES;
+  static constexpr bool LO_TERMS = (S == 4 || S == 6) && KAHAN;
+  static constexpr int RING_IN = ring_of(BUDGET_ - HEADER, MAIN_BYTES + (LO_TERMS ? 2 * IS_BYTES : 0));
+  static constexpr int RING_SPLIT = ring_of(BUDGET_ - HEADER - 3 * 2 * IS_BYTES, MAIN_BYTES);
+  static constexpr bool LOR = S == 6 && KAHAN && RING_IN <= 5 && RING_SPLIT > RING_IN;
+  static constexpr int NIS = (S == 1) ? 1 : ((LO_TERMS && !LOR) ? 2 : 0);
   static constexpr int OFF_HG = NHS * HS_BYTES;
   static constexpr int OFF_IS = OFF_HG + NHG * HG_BYTES;
   static constexpr int OFF_IG = OFF_IS + NIS * IS_BYTES;
   static constexpr int SLOT_BYTES = OFF_IG + NIG * IG_BYTES;
   static constexpr uint32_t TX_BYTES =
       (uint32_t)(NHS * HS_RAW + NHG * HG_RAW + NIS * IS_RAW + NIG * IG_RAW);
-  static constexpr int HEADER = 384;  // 2 x 16 mbarriers, flags
-  static constexpr int RING = cmax(4, cmin(16, (BUDGET_ - HEADER) / SLOT_BYTES));
-  static constexpr int SMEM = HEADER + RING * SLOT_BYTES;
+  static constexpr int LO_BAR = 36;  // compensation full barriers at header byte 288, empty at 320
+  static constexpr int LO_SLOT = LOR ? 2 * IS_BYTES : 0;
+  static constexpr uint32_t LO_TX = LOR ? (uint32_t)(2 * IS_RAW) : 0u;
+  static constexpr int RING_LO = LOR ? 3 : 0;  // compensation slots (lead of two planes)
+  static constexpr int RING = LOR ? RING_SPLIT : RING_IN;
+  static constexpr int OFF_LO = HEADER + RING * SLOT_BYTES;  // compensation ring
+  static constexpr int SMEM = OFF_LO + RING_LO * LO_SLOT;
+  static_assert(SLOT_BYTES == MAIN_BYTES + NIS * IS_BYTES, "slot composition");
   static_assert(SMEM <= 227 * 1024, "ring of 4 slots does not fit in 227 KB of shared memory");
+  static_assert(RING_LO <= 4 && 8 * (LO_BAR + 4 + RING_LO) <= HEADER, "barrier area");
   static constexpr int MINB = MINB_;  // blocks per SM the registers must allow
   static constexpr bool ROTATE = PR::ROTATE;
   // packed FP32 arithmetic for pairs of x points (FP32 math, even VEC, difference form)
@@ -304,6 +323,11 @@ __device__ __forceinline__ void produce(const StageParams &prm, uint64_t *full, 
   int slot = 0;
   uint32_t fill = 0;  // fill count of `slot` (phase = fill & 1)
   uint32_t issued_slots = 0;
+  // compensation ring (stages 3+4): slot, fill count, slots ever filled
+  uint64_t *lo_full = full + C::LO_BAR, *lo_empty = full + C::LO_BAR + 4;
+  unsigned char *lo_ring = ring - C::HEADER + C::OFF_LO;
+  int lslot = 0;
+  uint32_t lfill = 0, lo_issued = 0;
   bool bad = false;
   for (int it = blockIdx.x; it < nitems && !bad; it += gridDim.x) {
     const WorkItem w = prm.items[it];
@@ -340,7 +364,7 @@ __device__ __forceinline__ void produce(const StageParams &prm, uint64_t *full, 
       if constexpr (S == 6) {
         tma_load_3d(base + C::OFF_HG, tm + TM_G1_H, bar, x0, y0, z);
         tma_load_3d(base + C::OFF_HG + C::HG_BYTES, tm + TM_G2_H, bar, x0, y0, z);
-        if constexpr (C::KAHAN) {
+        if constexpr (C::KAHAN && !C::LOR) {
           tma_load_3d(base + C::OFF_IS, mlp, bar, x0 + HXS, y0 + 2, z);
           tma_load_3d(base + C::OFF_IS + C::IS_BYTES, mlq, bar, x0 + HXS, y0 + 2, z);
         }
@@ -356,6 +380,23 @@ __device__ __forceinline__ void produce(const StageParams &prm, uint64_t *full, 
       }
       issued_slots |= 1u << slot;
       if (++slot == RING) { slot = 0; ++fill; }
+      if constexpr (C::LOR) {
+        // the compensation terms of output plane m - 2 (needed at step m);
+        // the slot's previous tile was consumed at step m - 3
+        if (m >= 4) {
+          if (lfill >= 1 && !mbar_wait_bounded(&lo_empty[lslot], (lfill - 1) & 1u)) { bad = true; break; }
+          int zl = z0 - 4 + m;
+          if (zwrap) zl = (zl % nz + nz) % nz;
+          zl += zoff;
+          unsigned char *lb = lo_ring + lslot * C::LO_SLOT;
+          uint64_t *lbar = &lo_full[lslot];
+          mbar_expect_tx(lbar, C::LO_TX);
+          tma_load_3d(lb, mlp, lbar, x0 + HXS, y0 + 2, zl);
+          tma_load_3d(lb + C::IS_BYTES, mlq, lbar, x0 + HXS, y0 + 2, zl);
+          lo_issued |= 1u << lslot;
+          if (++lslot == C::RING_LO) { lslot = 0; ++lfill; }
+        }
+      }
     }
   }
   if (bad) {
@@ -368,6 +409,11 @@ __device__ __forceinline__ void produce(const StageParams &prm, uint64_t *full, 
     if (!(issued_slots >> r & 1u)) continue;
     const uint32_t f = r < slot ? fill : fill - 1;
     (void)mbar_wait_bounded(&full[r], f & 1u);
+  }
+  for (int r = 0; r < C::RING_LO; ++r) {
+    if (!(lo_issued >> r & 1u)) continue;
+    const uint32_t f = r < lslot ? lfill : lfill - 1;
+    (void)mbar_wait_bounded(&lo_full[r], f & 1u);
   }
 }
 
@@ -625,8 +671,8 @@ struct Consumer {
   // is shifted by one plane first and the newest plane is at index 4.
   template <int ROT>
   __device__ __forceinline__ void plane(const Item &it, int m, int slot, int s2,
-                                        TM (&win)[5][KN][VY][VEC], TM &run_max,
-                                        bool &bad) const {
+                                        const unsigned char *lob, TM (&win)[5][KN][VY][VEC],
+                                        TM &run_max, bool &bad) const {
     constexpr int R0 = ROT < 0 ? 4 : ROT;
     constexpr int W0 = R0 % 5, WM1 = (R0 + 4) % 5, WM2 = (R0 + 3) % 5, WM3 = (R0 + 2) % 5,
                   WM4 = (R0 + 1) % 5;
@@ -710,7 +756,11 @@ struct Consumer {
 #pragma unroll
         for (int j = 0; j < VEC; ++j) X[j] = g2[j];
       }
-      if constexpr ((S == 4 || S == 6) && C::KAHAN) {
+      if constexpr (C::LOR) {  // compensation terms of plane z, from their own ring
+        const TS *is = reinterpret_cast<const TS *>(lob) + ioff;
+        load_as<TS, TM, VEC>(is, lp);
+        load_as<TS, TM, VEC>(is + C::IS_BYTES / (int)sizeof(TS), lq);
+      } else if constexpr ((S == 4 || S == 6) && C::KAHAN) {
         const TS *is = reinterpret_cast<const TS *>(b2 + C::OFF_IS) + ioff;
         load_as<TS, TM, VEC>(is, lp);
         load_as<TS, TM, VEC>(is + C::IS_BYTES / (int)sizeof(TS), lq);
@@ -905,6 +955,10 @@ struct Consumer {
     const int nitems = *prm.nitems;
     int slot = 0;
     uint32_t phase = 0;
+    uint64_t *lo_full = full + C::LO_BAR, *lo_empty = full + C::LO_BAR + 4;
+    const unsigned char *lo_ring = ring_ - C::HEADER + C::OFF_LO;
+    int lslot = 0;
+    uint32_t lphase = 0;
     const Desc *coef_d = nullptr;
     long long coef_n = -1;
     for (int itx = blockIdx.x; itx < nitems; itx += gridDim.x) {
@@ -972,15 +1026,24 @@ struct Consumer {
           atomicOr(prm.err, (unsigned)DEV_ERR_TIMEOUT);
           return false;
         }
+        const bool lo = C::LOR && m >= 4;  // an output plane: its compensation slot
+        if (lo && !mbar_wait_bounded(&lo_full[lslot], lphase)) {
+          *abort_flag = 1;
+          atomicOr(prm.err, (unsigned)DEV_ERR_TIMEOUT);
+          return false;
+        }
         if (*abort_flag) return false;
         const int s2 = slot >= 2 ? slot - 2 : slot + RING - 2;  // slot of plane m - 2
-        self.template plane<decltype(rot)::value>(it, m, slot, s2, win, run_max, bad);
+        self.template plane<decltype(rot)::value>(it, m, slot, s2, lo_ring + lslot * C::LO_SLOT,
+                                                  win, run_max, bad);
         __syncwarp();
         if (self.lane == 0) {
           if (m < 2 || m >= it.nplanes - 2) mbar_arrive(&empty[slot]);
           if (m >= 4) mbar_arrive(&empty[s2]);
+          if (lo) mbar_arrive(&lo_empty[lslot]);
         }
         if (++slot == RING) { slot = 0; phase ^= 1u; }
+        if (lo && ++lslot == C::RING_LO) { lslot = 0; lphase ^= 1u; }
         return true;
       };
       bool ok = true;
@@ -1028,6 +1091,10 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
     for (int r = 0; r < C::RING; ++r) {
       mbar_init(&full[r], 1);
       mbar_init(&empty[r], C::NW);
+    }
+    for (int r = 0; r < C::RING_LO; ++r) {
+      mbar_init(&full[C::LO_BAR + r], 1);
+      mbar_init(&full[C::LO_BAR + 4 + r], C::NW);
     }
     *abort_flag = 0;
     fence_barrier_init();

@@ -28,9 +28,9 @@ const VariantTable &variants_fp32() {
     using PR = PrecFP32;
     VariantTable t{};
     // <precision, x points per lane, rows per warp, consumer warps, smem budget, min blocks/SM>
-    add<PR, 4, 1, 11, 220 * 1024, 1>(t);  // 128 x 11 tile, 12 warps, one CTA per SM
+    add<PR, 4, 1, 11, 226 * 1024, 1>(t);  // 128 x 11 tile, 12 warps, one CTA per SM
     // the same, with stages 1+2 on a 128 x 15 tile, 16 warps at <= 128 registers
-    add<PR, 4, 1, 11, 220 * 1024, 1, 15>(t);
+    add<PR, 4, 1, 11, 226 * 1024, 1, 15>(t);
     add<PR, 4, 1, 8, 220 * 1024, 1>(t);   // 128 x 8 tile, 9 warps, one CTA per SM
     add<PR, 2, 1, 11, 220 * 1024, 1>(t);  // 64 x 11 tile, 12 warps, one CTA per SM
     add<PR, 2, 1, 4, 110 * 1024, 2>(t);   // 64 x 4 tile, 5 warps, two CTAs per SM
