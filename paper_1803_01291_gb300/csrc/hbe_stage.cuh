@@ -146,13 +146,14 @@ struct StageCfg {
   // one row per warp with packed arithmetic: the 13-point sums are formed part
   // by part (z pairs, rows +-1, rows +-2, x pairs), so fewer neighbour values
   // are live at once
-  static constexpr bool INCR = PACKED && VY_ == 1 && S_ == 5;
-  // stages 1+2: the x neighbours of both stage arguments are formed from the
+  static constexpr bool INCR = PACKED && VY_ == 1 && PAIR;
+  // fused pairs: the x neighbours of both stage arguments are formed from the
   // ring's halo columns by every lane instead of exchanged by warp shuffles
-  static constexpr bool XLDS = PACKED && S_ == 5;
-  // stage arguments formed by packed FMAs (stages 1+2; the stages 3+4 kernel,
-  // which holds the compensated state, spills with them)
-  static constexpr bool PCOMB = PACKED && S_ == 5;
+  static constexpr bool XLDS = PACKED && PAIR;
+  // fused pairs: stage arguments formed by packed FMAs.  In the stages 3+4
+  // kernel each of these three alone spills on the 128 x 11 tile; together
+  // they fit (158 registers FP32, 156 BF16)
+  static constexpr bool PCOMB = PACKED && PAIR;
   // stages 1+2 with the Laplacian monitor of Sec. 3: max over the grid of
   // |Delta_h phi| of the step's starting state (stage 1's argument is phi)
   static constexpr bool MON = MON_ && S_ == 5;
