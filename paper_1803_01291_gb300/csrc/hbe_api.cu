@@ -348,6 +348,13 @@ const void *pinned_device_ptr(const void *host) {
   return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
+// Test hook for the bounded waits (HBE_DEBUG_WITHHOLD_PLANE set and not "0",
+// read at each context creation): see Desc::withhold.
+bool withhold_plane() {
+  const char *v = std::getenv("HBE_DEBUG_WITHHOLD_PLANE");
+  return v && *v && std::strcmp(v, "0") != 0;
+}
+
 bool nan_canary(const hbe_ctx *ctx) {
   if (ctx->bc != HBE_BC_PERIODIC) return false;
   const char *v = std::getenv("HBE_DEBUG_NAN_GHOSTS");
@@ -585,6 +592,7 @@ hbe_status create_common(int N, double L, double mu, double lambda, int bc, int 
   d.N = N; d.bc = bc; d.prec = prec;
   d.nz = ctx->nz; d.zoff = ctx->zoff;
   d.zwrap = (bc == HBE_BC_PERIODIC && ctx->zoff == 0) ? 1 : 0;
+  d.withhold = withhold_plane() ? 1 : 0;
   d.pitch_s = ctx->pitch_s; d.pitch_g = ctx->pitch_g;
   d.plane_s = ctx->plane_s; d.plane_g = ctx->plane_g;
   d.inv_h2 = 1.0 / (ctx->h * ctx->h);

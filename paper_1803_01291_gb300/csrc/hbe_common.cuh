@@ -71,8 +71,11 @@ struct alignas(64) Desc {
   // z extent of the stored block: nz interior planes starting at storage plane
   // zoff (a z-slab keeps zoff = 2 halo planes on each side, filled by the halo
   // exchange); zwrap = 1 wraps z-plane indices (a periodic context stored
-  // whole), else planes outside the storage read as zero
-  int32_t nz, zoff, zwrap, pad2;
+  // whole), else planes outside the storage read as zero.  withhold = 1 (a
+  // test hook, 0 in normal use): the stages 1+2 producer of block 0 never
+  // issues the first plane of its first work item, so the consumers' bounded
+  // waits on a barrier nothing completes run out (HBE_ETIMEOUT)
+  int32_t nz, zoff, zwrap, withhold;
   int32_t pitch_s, pitch_g;      // padded row pitch (elements) of state / G fields
   int64_t plane_s, plane_g;      // elements per padded z-plane
   double inv_h2, mu2, lambda;

@@ -352,6 +352,12 @@ __device__ __forceinline__ void produce(const StageParams &prm, uint64_t *full, 
     for (int m = 0; m < nplanes; ++m) {
       if (fill >= 1 && !mbar_wait_bounded(&empty[slot], (fill - 1) & 1u)) { bad = true; break; }
       if (*abort_flag) { bad = true; break; }
+      if constexpr (S == 5) {
+        if (d->withhold && blockIdx.x == 0 && it == 0 && m == 0) {  // test hook (Desc::withhold)
+          if (++slot == RING) { slot = 0; ++fill; }
+          continue;
+        }
+      }
       unsigned char *base = ring + slot * C::SLOT_BYTES;
       uint64_t *bar = &full[slot];
       int z = z0 - 2 + m;

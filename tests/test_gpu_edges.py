@@ -1,9 +1,11 @@
 """Edge cases through the C ABI: zero steps, the smallest grid the library
 accepts, a grid too large for the device (a clean HBE_ENOMEM, the library
-still usable afterwards), and the largest FP32 grid that fits on one GB300,
-checked by an invariant that holds at any size (data even in x, y and z on
-the symmetric grid of Sec. 2.1 stays even, bit for bit)."""
+still usable afterwards), a stage kernel whose bounded wait runs out (a clean
+HBE_ETIMEOUT), and the largest FP32 grid that fits on one GB300, checked by an
+invariant that holds at any size (data even in x, y and z on the symmetric
+grid of Sec. 2.1 stays even, bit for bit)."""
 import ctypes
+import time
 
 import numpy as np
 import pytest
@@ -85,6 +87,30 @@ def test_grid_larger_than_the_device_fails_cleanly(hbe):
     ctx = ctypes.c_void_p()
     st = lib.hbe_create(2048, 20.0, 1.0, 1.0, 0, hbe.FP32, ctypes.byref(ctx))
     assert st == hbe._lib.ENOMEM and not ctx.value
+    test_smallest_grid_matches_oracle(hbe, 0, 1, 2e-5)
+
+
+def test_withheld_plane_times_out_cleanly(hbe, monkeypatch):
+    """With HBE_DEBUG_WITHHOLD_PLANE set at creation, the stages 1+2 producer
+    of block 0 never issues the first plane of its first work item: its
+    consumers wait on a barrier that nothing completes, give up after their
+    bound (~2 s), and the step returns HBE_ETIMEOUT instead of hanging.  The
+    library keeps working: a new context matches the oracle."""
+    monkeypatch.setenv("HBE_DEBUG_WITHHOLD_PLANE", "1")
+    N = 16
+    phi0, phi1 = rand_fields(N, 0, 5)
+    s = hbe.Solver(N, 4.0, 1.0, 1.0, 0, hbe.FP32)
+    try:
+        s.set_initial(phi0, phi1)
+        t0 = time.perf_counter()
+        with pytest.raises(hbe._lib.HBEError) as e:
+            s.step(1, hi.grid_spacing(N, 4.0, 0) / 4)
+        waited = time.perf_counter() - t0
+    finally:
+        s.close()
+    assert e.value.status == hbe._lib.ETIMEOUT
+    assert 1.0 < waited < 60.0
+    monkeypatch.delenv("HBE_DEBUG_WITHHOLD_PLANE")
     test_smallest_grid_matches_oracle(hbe, 0, 1, 2e-5)
 
 
