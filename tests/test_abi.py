@@ -73,3 +73,28 @@ def test_product_never_imports_the_oracle():
                 text = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in text and "from oracle" not in text, fn
                 assert "hbe_oracle" not in text, fn
+
+
+def test_stage_rings_fit_and_keep_planes_in_flight(lib):
+    """The variant table (static, readable without a GPU): every stage kernel
+    fits the 227 KB of shared memory a block may use, and every fused stages
+    3+4 kernel of the memory-bound FP32-math precisions keeps at least two
+    planes in flight (a ring slot is held for three plane steps, so ring >= 5;
+    the FP64 kernels are bound by the FP64 pipe instead and keep 4 slots in a
+    110 KB budget).  The FP32 128 x 11 tile's stages 3+4
+    kernel, whose 44 KB slots with the compensation tiles inside would allow
+    only 5, holds six 32 KB slots (phi, psi, G1, G2 halo tiles of 15 x 136
+    floats, 128-byte aligned) and a ring of three 11 KB slots of compensation
+    tiles (11 x 128 floats each) after a 384-byte header."""
+    from paper_1803_01291_gb300 import solver
+    limit = 227 * 1024
+    for prec in (_lib.FP64, _lib.FP32, _lib.BF16, _lib.FP32_PLAIN):
+        for v in solver.variants(prec):
+            assert max(v["smem"]) <= limit and max(v["pair_smem"]) <= limit
+            assert v["pair_ring"][1] >= (4 if prec == _lib.FP64 else 5), (prec, v)
+    v0 = solver.variants(_lib.FP32)[0]
+    assert (v0["tile_x"], v0["pair_tile_y"][1]) == (128, 11)
+    halo = (15 * 136 * 4 + 127) // 128 * 128
+    comp = 2 * 11 * 128 * 4
+    assert v0["pair_ring"][1] == 6
+    assert v0["pair_smem"][1] == 384 + 6 * 4 * halo + 3 * comp
