@@ -285,88 +285,61 @@ def e2e_solve(hbe, torch, prob, prec_id, nsteps, solves=3, buffers=None):
     return total, st, float(np.abs(out.numpy()).max()), phases
 
 
-def e2e_solve_pipelined(hbe, torch, prob, prec_id, nsteps, solves=3, buffers=None):
-    """`solves` back-to-back solves through the public API, as a user streaming
-    problems through one context would run them: while solve k steps, solve
-    k+1's phi0, phi1 go from pinned host memory to device staging tensors by
-    DMA on a copy stream (then `set_initial` packs them on the device), and
-    solve k-1's phi, unpacked by `read_device`, goes back to pinned host memory
-    the same way.  The first solve's inputs and the last solve's phi, which
-    nothing overlaps, take the library's direct path (the pack / unpack kernels
-    read and write the pinned host arrays).  Every copy is inside the timed
-    region.  Returns the total time and the critical-path phases of each solve."""
+def e2e_solve_pipelined(hbe, torch, prob, prec_id, nsteps, solves=5, buffers=None):
+    """`solves` back-to-back solves through the C ABI with host buffers, as a
+    user streaming problems through one context runs them: while solve k
+    steps, solve k+1's phi0, phi1 are prefetched from pinned host memory
+    (`hbe_prefetch_initial`, DMA on the context's copy stream) and solve k-1's
+    phi, read with `hbe_read_async`, crosses back to pinned host memory the
+    same way.  The first solve's inputs and the last solve's phi, which nothing
+    overlaps, take the direct path (the pack / unpack kernels read and write
+    the pinned host arrays).  Every copy is inside the timed region.  Returns
+    the total time and the critical-path phases of each solve."""
     import numpy as np
     import ctypes
     N = prob.N
     h0, h1, out = buffers if buffers is not None else e2e_buffers(torch, prob)
+    a0, a1, o = h0.numpy(), h1.numpy(), out.numpy()
     s = hbe.Solver(N, prob.L, prob.mu, prob.lam, prob.bc, prec_id)
-    comp, copy = torch.cuda.Stream(), torch.cuda.Stream()
-    s.set_stream(comp.cuda_stream)
-    shape = (N, N, N)
-    d_in = [(torch.empty(shape, dtype=torch.float64, device="cuda"),
-             torch.empty(shape, dtype=torch.float64, device="cuda")) for _ in range(2)]
-    d_out = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(2)]
-    in_ready = [torch.cuda.Event() for _ in range(2)]
-    out_done = [torch.cuda.Event() for _ in range(2)]
     tt = ctypes.c_double()
     dp = ctypes.POINTER(ctypes.c_double)
 
-    def load(k):  # inputs of solve k into staging set k % 2
-        with torch.cuda.stream(copy):
-            d_in[k % 2][0].copy_(h0, non_blocking=True)
-            d_in[k % 2][1].copy_(h1, non_blocking=True)
-            in_ready[k % 2].record(copy)
+    def read_direct():
+        s.lib.hbe_read(s.handle, ctypes.cast(out.data_ptr(), dp), None, ctypes.byref(tt))
 
-    def store(k):  # phi of solve k (unpacked and synchronised) to the host
-        with torch.cuda.stream(copy):
-            out.copy_(d_out[k % 2], non_blocking=True)
-            out_done[k % 2].record(copy)
-
-    # warm (graph capture, both paths, both copy directions)
-    load(0)
-    in_ready[0].synchronize()
-    s.set_initial(d_in[0][0], d_in[0][1])
+    # warm (graph capture, staging areas, both paths and directions)
+    s.prefetch_initial(a0, a1)
+    s.set_initial_prefetched()
     s.step(2, prob.dt)
-    s.read_device(d_out[0])
-    s.sync()
-    store(0)
-    s.set_initial(h0.numpy(), h1.numpy())
-    s.lib.hbe_read(s.handle, ctypes.cast(out.data_ptr(), dp), None, ctypes.byref(tt))
+    s.read_async(o)
+    s.read_wait()
+    s.set_initial(a0, a1)
+    read_direct()
     torch.cuda.synchronize()
     phases, st = [], 0
     t_start = time.perf_counter()
     for k in range(solves):
         t0 = time.perf_counter()
         if k == 0:
-            s.set_initial(h0.numpy(), h1.numpy())
+            s.set_initial(a0, a1)
         else:
-            in_ready[k % 2].synchronize()
-            s.set_initial(d_in[k % 2][0], d_in[k % 2][1])
+            s.set_initial_prefetched()
         t1 = time.perf_counter()
         s.step_async(nsteps, prob.dt)
-        # both copies are issued while this solve's steps run (a copy call may
-        # block the host until its transfer ends)
         if k + 1 < solves:
-            load(k + 1)
-        if k >= 1:
-            store(k - 1)     # unpacked and synchronised at the end of solve k-1
+            s.prefetch_initial(a0, a1)   # overlaps this solve's steps
         st = s.sync()
         t2 = time.perf_counter()
-        if k < solves - 1:
-            if k >= 2:
-                out_done[k % 2].synchronize()  # staging tensor k % 2 was read back
-            s.read_device(d_out[k % 2])
-            s.sync()
+        if k + 1 < solves:
+            s.read_async(o)              # its copy overlaps the next solve
         else:
-            copy.synchronize()  # earlier solves' phi are home before the last overwrites it
-            s.lib.hbe_read(s.handle, ctypes.cast(out.data_ptr(), dp), None, ctypes.byref(tt))
+            s.read_wait()
+            read_direct()
         t3 = time.perf_counter()
         phases.append({"initial_data_s": t1 - t0, "steps_s": t2 - t1, "read_s": t3 - t2})
-    copy.synchronize()
-    torch.cuda.synchronize()
     total = time.perf_counter() - t_start
     s.close()
-    return total, st, float(np.abs(out.numpy()).max()), phases
+    return total, st, float(np.abs(o).max()), phases
 
 
 def serve_leg(hbe, count: int = 256, seed: int = 0, load: float = 0.8):
@@ -653,11 +626,12 @@ def main():
                        "d2h_bytes_per_step": 8 * N ** 3 / nsteps,
                        "steps_per_solve": nsteps, "solves": solves,
                        "phases": phases,
-                       "note": "back-to-back solves through one context, each: phi0, phi1 from "
-                               "pinned host, nsteps RK4 steps, phi to pinned host; the next "
-                               "solve's inputs and the previous solve's phi cross the host link "
-                               "by DMA while a solve steps (the first solve's inputs and the last "
-                               "one's phi on the direct path); bytes amortised per RK4 step",
+                       "note": "back-to-back solves through one context and the C ABI with "
+                               "pinned host buffers, each: phi0, phi1 in, nsteps RK4 steps, phi "
+                               "out; the next solve's inputs (hbe_prefetch_initial) and the "
+                               "previous solve's phi (hbe_read_async) cross the host link by DMA "
+                               "while a solve steps, the first inputs and the last phi on the "
+                               "direct path; bytes amortised per RK4 step",
                        "sequential": {
                            "value": float(N) ** 3 * nsteps * seq_solves * world / seq_secs / 1e9,
                            "solves": seq_solves, "phases": seq_phases,

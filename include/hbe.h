@@ -176,6 +176,35 @@ hbe_status hbe_sync(hbe_ctx *ctx);
 hbe_status hbe_read(hbe_ctx *ctx, double *phi, double *psi, double *t);
 /* Same to device arrays on the context's stream (not synchronised). */
 hbe_status hbe_read_device(hbe_ctx *ctx, double *d_phi, double *d_psi);
+
+/* Streaming host I/O, for a sequence of problems solved one after another on
+ * one context (the Cauchy data of Sec. 1 in, phi out) with the host-link
+ * transfers overlapped with the neighbouring problems' steps.
+ *
+ * hbe_prefetch_initial starts copying phi0, phi1 (caller-owned host arrays of
+ * N^3 doubles, [z][y][x] as for hbe_set_initial) into a device staging area of
+ * the context by DMA on its copy stream and returns; page-locked arrays are
+ * needed for the copy to overlap anything.  The current state is not touched,
+ * so it may be called while hbe_step_async steps.  The arrays must stay
+ * unchanged until hbe_set_initial_prefetched.  A second call before that
+ * replaces the first.  The staging area (2 N^3 doubles) is allocated at the
+ * first call and kept until hbe_destroy: HBE_ENOMEM if it does not fit.
+ *
+ * hbe_set_initial_prefetched(ctx, t0) makes the prefetched arrays the initial
+ * data at time t0, as hbe_set_initial would; it waits for the copy and blocks.
+ * HBE_ESTATE if nothing was prefetched.
+ *
+ * hbe_read_async waits for the steps taken (as hbe_read does), unpacks phi
+ * (and psi if non-null; one of the two may be null) into a second staging
+ * area on the context's stream, starts their copy to the caller's host arrays
+ * (N^3 doubles each, page-locked for the copy to overlap) and returns.  Work
+ * enqueued on the context afterwards (steps, new initial data) runs after the
+ * unpack; the host arrays hold the values once hbe_read_wait returns.  A
+ * second hbe_read_async first waits for the previous copy. */
+hbe_status hbe_prefetch_initial(hbe_ctx *ctx, const double *phi0, const double *phi1);
+hbe_status hbe_set_initial_prefetched(hbe_ctx *ctx, double t0);
+hbe_status hbe_read_async(hbe_ctx *ctx, double *phi, double *psi);
+hbe_status hbe_read_wait(hbe_ctx *ctx);
 /* Profiling aid: nsteps (1..4096) RK4 steps with the step's kernels launched
  * one at a time (no graph), each bracketed by CUDA events on the context's
  * stream; ms_per_stage[i] receives the mean duration of the i-th launch of a

@@ -20,7 +20,8 @@ EXPORTS = (
     "hbe_workspace_bytes", "hbe_create", "hbe_create_in", "hbe_destroy", "hbe_set_stream",
     "hbe_set_tuning", "hbe_set_schedule", "hbe_variant_info", "hbe_variant_count", "hbe_set_initial",
     "hbe_set_initial_device", "hbe_set_initial_bumps", "hbe_set_stop", "hbe_step", "hbe_step_async", "hbe_sync",
-    "hbe_read", "hbe_read_device", "hbe_profile_stages", "hbe_progress", "hbe_analysis", "hbe_set_monitor",
+    "hbe_read", "hbe_read_device", "hbe_prefetch_initial", "hbe_set_initial_prefetched",
+    "hbe_read_async", "hbe_read_wait", "hbe_profile_stages", "hbe_progress", "hbe_analysis", "hbe_set_monitor",
     "hbe_monitor_read", "hbe_diag", "hbe_save", "hbe_load",
     "hbe_last_error", "hbe_status_string", "hbe_launch_count", "hbe_batch_create",
     "hbe_batch_destroy", "hbe_batch_add", "hbe_batch_remove", "hbe_batch_run", "hbe_batch_launch",
@@ -101,6 +102,10 @@ def load() -> ctypes.CDLL:
             "hbe_sync": (I, [P]),
             "hbe_read": (I, [P, dp, dp, dp]),
             "hbe_read_device": (I, [P, P, P]),
+            "hbe_prefetch_initial": (I, [P, dp, dp]),
+            "hbe_set_initial_prefetched": (I, [P, D]),
+            "hbe_read_async": (I, [P, dp, dp]),
+            "hbe_read_wait": (I, [P]),
             "hbe_progress": (I, [P, ctypes.POINTER(I64), dp]),
             "hbe_profile_stages": (I, [P, I64, D, ctypes.POINTER(ctypes.c_float)]),
             "hbe_diag": (I, [P, D, ctypes.POINTER(HbeDiag), P, P]),

@@ -93,6 +93,12 @@ struct hbe_ctx {
   size_t stage_elems = 0;
   cudaStream_t copy_stream = nullptr;   // host <-> staging copies
   cudaEvent_t ev_ready[2] = {}, ev_free[2] = {};
+  // streaming host I/O (hbe_prefetch_initial, hbe_read_async): whole-field
+  // staging areas of 2 N^3 doubles each, allocated at first use
+  double *d_pre = nullptr, *d_rout = nullptr;
+  cudaEvent_t ev_pre = nullptr, ev_rout_ready = nullptr, ev_rout_done = nullptr;
+  bool pre_pending = false;    // a prefetch not yet consumed
+  bool rout_pending = false;   // a read whose copy to the host may still run
   uint32_t *d_masks = nullptr;
   int *d_labels = nullptr;
   unsigned long long *d_counts = nullptr;
@@ -644,6 +650,7 @@ hbe_status hbe_create_in(int N, double L, double mu, double lambda, int bc, int 
 void hbe_destroy(hbe_ctx *ctx) {
   if (!ctx) return;
   if (ctx->stream || ctx->cap_stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
   drop_graphs(ctx);
   if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
   cudaFree(ctx->d_tmaps);
@@ -658,6 +665,10 @@ void hbe_destroy(hbe_ctx *ctx) {
   cudaFree(ctx->d_one);
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_stage);
+  cudaFree(ctx->d_pre);
+  cudaFree(ctx->d_rout);
+  for (cudaEvent_t e : {ctx->ev_pre, ctx->ev_rout_ready, ctx->ev_rout_done})
+    if (e) cudaEventDestroy(e);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   for (int b = 0; b < 2; ++b) {
     if (ctx->ev_ready[b]) cudaEventDestroy(ctx->ev_ready[b]);
@@ -1064,6 +1075,96 @@ hbe_status hbe_read_device(hbe_ctx *ctx, double *d_phi, double *d_psi) {
   hbe_status st = sync_ctx(ctx);
   if (st != HBE_OK) return st;
   return read_impl(ctx, d_phi, d_psi, true);
+}
+
+// ---------------------------------------------------------------- streaming host I/O
+// The next problem's initial data crosses the host link while the current one
+// steps, and a result crosses back while the next one steps: both by DMA on
+// the copy stream, through whole-field staging areas, so the context's stream
+// only packs and unpacks device memory.
+static hbe_status ensure_async_io(hbe_ctx *ctx, double **buf) {
+  if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  for (cudaEvent_t *e : {&ctx->ev_pre, &ctx->ev_rout_ready, &ctx->ev_rout_done})
+    if (!*e) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  if (!*buf) {
+    const size_t n = (size_t)ctx->N * ctx->N * ctx->N;
+    if (cudaMalloc(buf, 2 * n * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      *buf = nullptr;
+      return set_err(ctx->err, HBE_ENOMEM, "no device memory for a %zu-byte staging area",
+                     2 * n * sizeof(double));
+    }
+  }
+  return HBE_OK;
+}
+
+hbe_status hbe_prefetch_initial(hbe_ctx *ctx, const double *phi0, const double *phi1) {
+  Range range_("hbe_prefetch_initial");
+  if (!ctx || !phi0 || !phi1) return HBE_EINVAL;
+  if (ctx->in_batch) return set_err(ctx->err, HBE_ESTATE, "context is in a batch");
+  hbe_status st = ensure_async_io(ctx, &ctx->d_pre);
+  if (st != HBE_OK) return st;
+  const size_t n = (size_t)ctx->N * ctx->N * ctx->N;
+  CK(cudaMemcpyAsync(ctx->d_pre, phi0, n * sizeof(double), cudaMemcpyHostToDevice,
+                     ctx->copy_stream));
+  CK(cudaMemcpyAsync(ctx->d_pre + n, phi1, n * sizeof(double), cudaMemcpyHostToDevice,
+                     ctx->copy_stream));
+  CK(cudaEventRecord(ctx->ev_pre, ctx->copy_stream));
+  ctx->pre_pending = true;
+  return HBE_OK;
+}
+
+hbe_status hbe_set_initial_prefetched(hbe_ctx *ctx, double t0) {
+  Range range_("hbe_set_initial_prefetched");
+  if (!ctx) return HBE_EINVAL;
+  if (!ctx->pre_pending) return set_err(ctx->err, HBE_ESTATE, "no prefetched initial data");
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_pre, 0));
+  const size_t n = (size_t)ctx->N * ctx->N * ctx->N;
+  hbe_status st = set_initial_impl(ctx, ctx->d_pre, ctx->d_pre + n, t0, true);
+  if (st != HBE_OK) return st;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->pre_pending = false;
+  return HBE_OK;
+}
+
+hbe_status hbe_read_async(hbe_ctx *ctx, double *phi, double *psi) {
+  Range range_("hbe_read_async");
+  if (!ctx || (!phi && !psi)) return HBE_EINVAL;
+  if (!ctx->has_state) return set_err(ctx->err, HBE_ESTATE, "no initial data");
+  hbe_status st = sync_ctx(ctx);
+  if (st != HBE_OK) return st;
+  if ((st = ensure_async_io(ctx, &ctx->d_rout)) != HBE_OK) return st;
+  if (ctx->rout_pending) {  // the staging area still feeds the previous read's copy
+    CK(cudaEventSynchronize(ctx->ev_rout_done));
+    ctx->rout_pending = false;
+  }
+  const size_t n = (size_t)ctx->N * ctx->N * ctx->N;
+  // unpack on the context's stream (later work there is ordered after it),
+  // then the copy to the host once the unpack is done
+  if ((st = read_impl(ctx, phi ? ctx->d_rout : nullptr, psi ? ctx->d_rout + n : nullptr, true)) !=
+      HBE_OK)
+    return st;
+  CK(cudaEventRecord(ctx->ev_rout_ready, ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_rout_ready, 0));
+  if (phi)
+    CK(cudaMemcpyAsync(phi, ctx->d_rout, n * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->copy_stream));
+  if (psi)
+    CK(cudaMemcpyAsync(psi, ctx->d_rout + n, n * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->copy_stream));
+  CK(cudaEventRecord(ctx->ev_rout_done, ctx->copy_stream));
+  ctx->rout_pending = true;
+  return HBE_OK;
+}
+
+hbe_status hbe_read_wait(hbe_ctx *ctx) {
+  Range range_("hbe_read_wait");
+  if (!ctx) return HBE_EINVAL;
+  if (ctx->rout_pending) {
+    CK(cudaEventSynchronize(ctx->ev_rout_done));
+    ctx->rout_pending = false;
+  }
+  return HBE_OK;
 }
 
 hbe_status hbe_diag(hbe_ctx *ctx, double eps, hbe_diag_t *out, uint32_t *pos_mask,

@@ -194,6 +194,38 @@ class Solver:
                                     ps.ctypes.data_as(dp) if psi else None, ctypes.byref(t)))
         return phi, ps, t.value
 
+    @staticmethod
+    def _host_field(a, N):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.shape == (N,) * 3
+                and a.flags.c_contiguous):
+            raise ValueError("expected a C-contiguous float64 numpy array of shape (N, N, N)")
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    def prefetch_initial(self, phi0, phi1):
+        """Start copying host arrays phi0, phi1 (C-contiguous float64 (N, N, N);
+        page-locked memory lets the copy overlap the steps) into the context's
+        staging area and return; they become the initial data at the next
+        set_initial_prefetched and must not change until then."""
+        a, b = self._host_field(phi0, self.N), self._host_field(phi1, self.N)
+        self._chk(self.lib.hbe_prefetch_initial(self._ctx, a, b))
+        self._prefetched = (phi0, phi1)
+
+    def set_initial_prefetched(self, t0: float = 0.0):
+        self._chk(self.lib.hbe_set_initial_prefetched(self._ctx, t0))
+        self._prefetched = None
+
+    def read_async(self, phi_out, psi_out=None):
+        """Start reading phi (and psi) into the given host arrays and return;
+        they hold the state once read_wait() returns."""
+        a = self._host_field(phi_out, self.N)
+        b = self._host_field(psi_out, self.N) if psi_out is not None else None
+        self._chk(self.lib.hbe_read_async(self._ctx, a, b))
+        self._reading = (phi_out, psi_out)
+
+    def read_wait(self):
+        self._chk(self.lib.hbe_read_wait(self._ctx))
+        self._reading = None
+
     def read_device(self, phi_out=None, psi_out=None):
         """State into float64 torch CUDA tensors (allocated if not given)."""
         torch = _torch()
