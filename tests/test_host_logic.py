@@ -271,3 +271,92 @@ def test_reference_arm_is_silent_on_other_ranks(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     bench.reference_arm(_ref_args())
     assert capsys.readouterr().out == ""
+
+
+# ---------------------------------------------------------------- end-to-end harness
+class _Buf:
+    def __init__(self):
+        import numpy as _np
+        self.a = _np.zeros((2, 2, 2))
+
+    def numpy(self):
+        return self.a
+
+    def data_ptr(self):
+        return 0
+
+
+def test_pipelined_e2e_moves_every_solve_inside_the_timed_region():
+    """bench.e2e_solve_pipelined on a recording fake: every solve gets its
+    inputs (direct for the first, prefetched for the others), steps and sends
+    phi back (async for all but the last, direct for the last); each prefetch
+    is issued while a solve's steps are in flight (between step_async and
+    sync), each async read right after a solve's sync (its copy then overlaps
+    the next solve), and nothing is left pending when the clock stops."""
+    log = []
+
+    class Lib:
+        def hbe_read(self, *a):
+            log.append("read_direct")
+
+    class FakeSolver:
+        def __init__(self, *a):
+            self.lib, self.handle, self.stepping = Lib(), None, False
+
+        def set_initial(self, a, b):
+            log.append("set_initial")
+
+        def prefetch_initial(self, a, b):
+            log.append("prefetch" + ("*" if self.stepping else ""))
+
+        def set_initial_prefetched(self, t0=0.0):
+            log.append("set_prefetched")
+
+        def step(self, n, dt):
+            log.append("step")
+
+        def step_async(self, n, dt):
+            self.stepping = True
+            log.append("step_async")
+
+        def sync(self):
+            self.stepping = False
+            log.append("sync")
+            return 0
+
+        def read_async(self, o):
+            log.append("read_async")
+
+        def read_wait(self):
+            log.append("read_wait")
+
+        def close(self):
+            log.append("close")
+
+    class FakeHbe:
+        Solver = FakeSolver
+
+    class FakeTorch:
+        class cuda:
+            @staticmethod
+            def synchronize():
+                log.append("cuda_sync")
+
+    class Prob:
+        N, L, mu, lam, bc, dt = 2, 1.0, 1.0, 1.0, 0, 0.1
+
+    solves = 4
+    total, st, _, phases = bench.e2e_solve_pipelined(FakeHbe, FakeTorch, Prob, 1, 3, solves,
+                                                     (_Buf(), _Buf(), _Buf()))
+    timed = log[log.index("cuda_sync") + 1:]
+    assert len(phases) == solves and st == 0 and total >= 0
+    assert timed.count("step_async") == solves
+    assert timed[0] == "set_initial"                        # the first inputs: direct
+    assert timed.count("set_prefetched") == solves - 1       # the others: prefetched
+    assert timed.count("prefetch*") == solves - 1            # ... while a solve steps
+    assert "prefetch" not in timed
+    assert timed.count("read_async") == solves - 1           # phi of all but the last: async
+    assert timed[-3:] == ["read_wait", "read_direct", "close"]  # last phi direct, none pending
+    for k in range(solves - 1):                              # async reads follow a sync
+        i = [j for j, e in enumerate(timed) if e == "read_async"][k]
+        assert timed[i - 1] == "sync"
