@@ -24,7 +24,10 @@
  *     stage times are t_n, t_n + dt/2, t_n + dt/2, t_n + dt (Sec. 2.1).
  *   - Every call returns an hbe_status; nothing throws or aborts.  After an
  *     error, hbe_last_error() describes it.  A context is used by one host
- *     thread at a time.  No call keeps a pointer to caller memory.
+ *     thread at a time.  No call keeps a pointer to caller memory, except
+ *     hbe_prefetch_initial and hbe_read_async, whose copies run after they
+ *     return (see there: the arrays must stay valid until the matching
+ *     hbe_set_initial_prefetched or hbe_read_wait).
  *   - Device memory for the fields is allocated by hbe_create (cudaMalloc)
  *     unless the caller hands a buffer of hbe_workspace_bytes() bytes to
  *     hbe_create_in, which then allocates nothing on the device for fields.
