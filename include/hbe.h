@@ -116,6 +116,8 @@ hbe_status hbe_create(int N, double L, double mu, double lambda, int bc, int pre
 hbe_status hbe_create_in(int N, double L, double mu, double lambda, int bc, int prec,
                          void *d_workspace, size_t bytes, hbe_ctx **out);
 
+/* Waits for the context's work and copies, then releases everything it
+ * allocated (not a caller's hbe_create_in buffer).  NULL is a no-op. */
 void hbe_destroy(hbe_ctx *ctx);
 
 /* Stream (cudaStream_t) every later call of this context enqueues on; NULL
@@ -246,6 +248,8 @@ typedef struct {
   int64_t support_points;
   int64_t condition1_violations;
 } hbe_analysis_t;
+/* Fills *out (caller-owned) for the current state; eps >= 0 (HBE_EINVAL
+ * otherwise), HBE_ESTATE without initial data. */
 hbe_status hbe_analysis(hbe_ctx *ctx, double eps, hbe_analysis_t *out);
 
 /* The Laplacian monitor P(t) = e^{-2t} max|Delta_h phi| of Sec. 3 (Example
@@ -270,6 +274,9 @@ hbe_status hbe_monitor_read(hbe_ctx *ctx, int64_t first, int64_t count, double *
 hbe_status hbe_save(hbe_ctx *ctx, const char *path);
 hbe_status hbe_load(hbe_ctx *ctx, const char *path);
 
+/* Text of the context's last error ("" if none; "null context" for NULL),
+ * valid until the context's next call; the name of a status code ("HBE_OK",
+ * ...; "unknown" for any other value), static. */
 const char *hbe_last_error(const hbe_ctx *ctx);
 const char *hbe_status_string(int status);
 
